@@ -1,0 +1,170 @@
+"""Torch-facing wrapper of the C ABI: device memory and streams come from
+PyTorch, every walk step runs in libfw.so.
+
+    g = DeviceGraph.from_graph(fw_inputs.rmat(20), device="cuda")
+    paths, plen = g.walk("node2vec", starts, max_len=80, seed=42, mode="fast", p=2, q=0.5)
+"""
+
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import torch
+
+from . import _fw
+
+_P = ctypes.c_void_p
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else _P(t.data_ptr())
+
+
+def _i32(t, device):
+    if t is None:
+        return None
+    t = torch.as_tensor(t)
+    if t.dtype != torch.int32:
+        t = t.to(torch.int32)
+    return t.to(device).contiguous()
+
+
+def _stream_handle(stream) -> Optional[_P]:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return _P(stream.cuda_stream)
+
+
+class DeviceGraph:
+    """A CSR graph resident on one GPU, owned by the library (or borrowed)."""
+
+    def __init__(self, handle: _P, n: int, m: int, keep=()):
+        self._h = handle
+        self.n, self.m = n, m
+        self._keep = keep  # borrowed tensors stay alive with the graph
+
+    @classmethod
+    def from_tensors(cls, row_ptr, col, w_f32=None, w_u32=None, etype=None, borrow=False,
+                     validate=True, device="cuda") -> "DeviceGraph":
+        L = _fw.lib()
+        dev = torch.device(device)
+        ts = []
+        for t, dt in ((row_ptr, torch.int64), (col, torch.int32), (w_f32, torch.float32),
+                      (w_u32, torch.int32), (etype, torch.int8)):
+            if t is None:
+                ts.append(None)
+                continue
+            t = torch.as_tensor(t)
+            if t.dtype != dt:
+                t = t.view(dt) if t.element_size() == torch.empty(0, dtype=dt).element_size() else t.to(dt)
+            ts.append(t.to(dev).contiguous())
+        n = ts[0].numel() - 1
+        m = ts[1].numel()
+        flags = (_fw.FW_BORROW if borrow else _fw.FW_DEVICE_PTRS) | (0 if validate else _fw.FW_NO_VALIDATE)
+        h = _P()
+        with torch.cuda.device(dev):
+            _fw.check(L.fw_load_csr(ctypes.byref(h), n, m, *[_ptr(t) for t in ts], flags))
+        return cls(h, n, m, keep=tuple(ts) if borrow else ())
+
+    @classmethod
+    def from_graph(cls, g, device="cuda", borrow=False, validate=True) -> "DeviceGraph":
+        return cls.from_tensors(g.row_ptr, g.col, g.w_f32, g.w_u32, g.etype, borrow=borrow,
+                                validate=validate, device=device)
+
+    # ------------------------------------------------------------------ walks
+    def walk(self, algo, starts, max_len: int, seed: int, mode="exact", p=1.0, q=1.0, scale=2,
+             schema: Sequence[int] = (0, 1, 2, 3, 4), ppr_stop=0.2, lengths=None, prev=None, step0=None,
+             q_id0: int = 0, paths=None, path_len=None, stream=None):
+        """Run one batch of walks; returns (paths [n_q, max_len+1] int32, path_len [n_q] int32).
+
+        Tensors on the GPU are used in place; CPU tensors are staged by the
+        library (the call then returns with the results on the host)."""
+        algo = _fw.ALGOS.get(algo, algo)
+        prm = _fw.make_params(mode, p, q, scale, schema, ppr_stop)
+        st = torch.as_tensor(starts)
+        dev = st.device
+        st = _i32(st, dev)
+        n_q = st.numel()
+        if paths is None:
+            paths = torch.empty((n_q, max_len + 1), dtype=torch.int32, device=dev)
+        if path_len is None:
+            path_len = torch.empty(n_q, dtype=torch.int32, device=dev)
+        ln, pv, s0 = _i32(lengths, dev), _i32(prev, dev), _i32(step0, dev)
+        sh = _stream_handle(stream) if dev.type == "cuda" else None
+        _fw.check(_fw.lib().fw_walk_ex(self._h, algo, ctypes.byref(prm), _ptr(st), n_q, _ptr(ln), max_len,
+                                       seed & 0xFFFFFFFFFFFFFFFF, q_id0, _ptr(pv), _ptr(s0), _ptr(paths),
+                                       _ptr(path_len), sh))
+        return paths, path_len
+
+    def walk_multi(self, requests, stream=None):
+        """requests: list of dicts with keys algo, starts, max_len, seed, mode,
+        p, q, scale, schema, ppr_stop, lengths, prev, step0, q_id0, paths,
+        path_len (device tensors).  One launch for all; returns the list of
+        (paths, path_len)."""
+        arr = (_fw.Request * len(requests))()
+        outs, keep = [], []
+        for i, r in enumerate(requests):
+            st = _i32(r["starts"], "cuda")
+            n_q = st.numel()
+            L = int(r["max_len"])
+            paths = r.get("paths")
+            if paths is None:
+                paths = torch.empty((n_q, L + 1), dtype=torch.int32, device=st.device)
+            plen = r.get("path_len")
+            if plen is None:
+                plen = torch.empty(n_q, dtype=torch.int32, device=st.device)
+            ln, pv, s0 = (_i32(r.get(k), st.device) for k in ("lengths", "prev", "step0"))
+            keep += [st, ln, pv, s0]
+            q = arr[i]
+            q.algo = _fw.ALGOS.get(r["algo"], r["algo"])
+            q.params = _fw.make_params(r.get("mode", "exact"), r.get("p", 1.0), r.get("q", 1.0),
+                                       r.get("scale", 2), r.get("schema", (0, 1, 2, 3, 4)),
+                                       r.get("ppr_stop", 0.2))
+            q.starts, q.n_q, q.max_len = st.data_ptr(), n_q, L
+            q.lengths = ln.data_ptr() if ln is not None else None
+            q.prev = pv.data_ptr() if pv is not None else None
+            q.step0 = s0.data_ptr() if s0 is not None else None
+            q.seed = int(r["seed"]) & 0xFFFFFFFFFFFFFFFF
+            q.q_id0 = int(r.get("q_id0", 0))
+            q.paths, q.path_len = paths.data_ptr(), plen.data_ptr()
+            outs.append((paths, plen))
+        _fw.check(_fw.lib().fw_walk_multi(self._h, arr, len(requests), _stream_handle(stream)))
+        return outs
+
+    # ------------------------------------------------------------ management
+    def set_tuning(self, block_threads=0, slots=0, d_warp=0, ctas_per_sm=0):
+        t = _fw.Tuning(block_threads, slots, d_warp, ctas_per_sm)
+        _fw.check(_fw.lib().fw_set_tuning(self._h, ctypes.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = _fw.Tuning()
+        _fw.check(_fw.lib().fw_get_tuning(self._h, ctypes.byref(t)))
+        return {k: getattr(t, k) for k, _ in _fw.Tuning._fields_}
+
+    def stats(self) -> dict:
+        s = _fw.Stats()
+        _fw.check(_fw.lib().fw_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in _fw.Stats._fields_}
+
+    def stats_reset(self, stream=None):
+        _fw.check(_fw.lib().fw_stats_reset(self._h, _stream_handle(stream)))
+
+    def info(self) -> dict:
+        n, m, dm = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _fw.check(_fw.lib().fw_graph_info(self._h, *(ctypes.byref(x) for x in (n, m, dm, a, b, c))))
+        return {"n": n.value, "m": m.value, "d_max": dm.value, "has_f32": bool(a.value),
+                "has_u32": bool(b.value), "has_type": bool(c.value)}
+
+    def free(self):
+        if self._h:
+            _fw.lib().fw_free(self._h)
+            self._h = None
+            self._keep = ()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

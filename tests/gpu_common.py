@@ -1,0 +1,70 @@
+"""Helpers shared by the GPU tests: build the library, move graphs to the
+device, check walks for validity with torch ops on the device."""
+
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import fw_inputs as fi
+
+
+def need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+
+
+@functools.lru_cache(maxsize=None)
+def built():
+    from paper_2404_08364_gb300.build import build
+    return build()
+
+
+def device_graph(g, **kw):
+    need_gpu()
+    built()
+    from paper_2404_08364_gb300 import DeviceGraph
+    return DeviceGraph.from_graph(g, device="cuda", **kw)
+
+
+@functools.lru_cache(maxsize=None)
+def cached_graph(kind, scale=0, types_seed=None):
+    """Graphs generated once per session (on the GPU when it is there)."""
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    if kind == "chunglu":
+        return fi.chung_lu(device=dev).to("cpu")
+    return fi.rmat(scale, types_seed=types_seed, device=dev).to("cpu")
+
+
+def edge_lookup(g, dev="cuda"):
+    """Sorted keys u*n+v of every CSR entry (device) and the edge labels."""
+    rp = g.row_ptr.to(dev)
+    src = torch.repeat_interleave(torch.arange(g.n, device=dev), rp[1:] - rp[:-1])
+    keys = src * g.n + g.col.to(dev).to(torch.int64)
+    return keys, None if g.etype is None else g.etype.to(dev)
+
+
+def check_valid(g, paths, plen, algo, schema=(0, 1, 2, 3, 4), max_len=None):
+    """Every move is an edge; MetaPath moves carry schema[t mod len]; padding
+    is -1; a walk that stopped early stopped for a reason the rule allows."""
+    dev = paths.device
+    keys, et = edge_lookup(g, dev)
+    n_q, width = paths.shape
+    t = torch.arange(width, device=dev)[None, :]
+    valid = t < plen[:, None].to(torch.int64)
+    assert bool((paths[~valid] == -1).all()), "padding must be -1"
+    assert bool((plen >= 1).all())
+    u = paths[:, :-1].to(torch.int64)
+    v = paths[:, 1:].to(torch.int64)
+    mv = valid[:, 1:]
+    uu, vv = u[mv], v[mv]
+    k = uu * g.n + vv
+    pos = torch.searchsorted(keys, k)
+    pos = torch.clamp(pos, max=keys.numel() - 1)
+    assert bool((keys[pos] == k).all()), "a move is not an edge"
+    if algo == "metapath":
+        tt = torch.arange(width - 1, device=dev)[None, :].expand(n_q, -1)[mv]
+        want = torch.tensor(list(schema), device=dev, dtype=torch.int8)[tt % len(schema)]
+        assert bool((et[pos] == want).all()), "a MetaPath move has the wrong label"
+    return int(mv.sum())
