@@ -1,0 +1,350 @@
+"""Benchmark: walk steps/s of the GPU walk engine, with its HBM roofline, an
+end-to-end number through the C ABI with host buffers, and the CPU oracle's
+throughput on a bounded sample beside it.
+
+Default workload: node2vec p=1, q=2 (fast mode, FP32 weights) on the R-MAT
+scale-25 graph (edge factor 16, symmetrised, 1.07e9 CSR entries, int64 row
+offsets, int32 columns), walks of length 80, one query per vertex; one bench
+step = one launch over a batch of 2^22 of those queries (vertices
+v = k mod 8 for step k).  The graph (8.9 GB) is far larger than L2, so no L2
+flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line on rank 0.
+"""
+
+from __future__ import annotations
+
+import argparse
+import concurrent.futures as cf
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (scale, algo, p, q, mode, L, types)
+    "rmat25_node2vec": dict(scale=25, algo="node2vec", p=1.0, q=2.0, mode="fast", L=80, types=None,
+                            batch_log2=22, slices=8),
+    "rmat20_node2vec": dict(scale=20, algo="node2vec", p=2.0, q=0.5, mode="fast", L=80, types=None,
+                            batch_log2=20, slices=1),
+    "rmat20_node2vec_exact": dict(scale=20, algo="node2vec", p=2.0, q=0.5, mode="exact", L=80, types=None,
+                                  batch_log2=20, slices=1),
+    "rmat22_weighted": dict(scale=22, algo="weighted", p=1.0, q=1.0, mode="fast", L=80, types=None,
+                            batch_log2=22, slices=1),
+}
+
+
+def describe(w):
+    return (f"{w['algo']} p={w['p']:g} q={w['q']:g}, {w['mode']} mode, R-MAT scale {w['scale']} "
+            f"(a,b,c=.57,.19,.19, ef 16, symmetrised), L={w['L']}, "
+            f"{2 ** w['batch_log2']} queries per step (1/{w['slices']} of one query per vertex)")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def make_graph(w, device):
+    import fw_inputs as fi
+    t0 = time.time()
+    g = fi.rmat(w["scale"], types_seed=w["types"], device=device)
+    return g, time.time() - t0
+
+
+def slice_starts(n, k, slices, batch, device):
+    import torch
+    s = torch.arange(k % slices, n, slices, dtype=torch.int32, device=device)
+    return s[:batch]
+
+
+def cpu_oracle_sample(g_host, w, seconds=15.0, threads=None, seed=42):
+    """The CPU oracle (as it stands: exact-mode walker, one query per call
+    range) on a bounded sample of the workload's queries, on `threads` host
+    threads over disjoint query ranges.  Returns (steps/s, threads, description)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    csr = oracle.CSR(g_host)
+    prm = oracle.Params(p=w["p"], q=w["q"], scale=2)
+    threads = threads or os.cpu_count() or 1
+    n = g_host.n
+    # sample: queries spread over the whole vertex range (vertex ids 0, s, 2s, ...)
+    per_call = 8
+    total_steps = 0
+    calls = 0
+    t0 = time.time()
+    stride = max(1, n // 100003)
+
+    def run(ci):
+        st = np.arange(ci * per_call * stride, (ci + 1) * per_call * stride, stride, dtype=np.int32) % n
+        _, plen = oracle.walk_exact(csr, w["algo"], prm, st, w["L"], seed, q0=int(st[0]))
+        return int((plen - 1).sum())
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = []
+        ci = 0
+        while time.time() - t0 < seconds:
+            while len(futs) < 2 * threads:
+                futs.append(ex.submit(run, ci))
+                ci += 1
+            done, _ = cf.wait(futs, return_when=cf.FIRST_COMPLETED)
+            for f in done:
+                total_steps += f.result()
+                calls += 1
+                futs.remove(f)
+        for f in futs:
+            total_steps += f.result()
+            calls += 1
+    dt = time.time() - t0
+    desc = (f"oracle (exact-mode C walker) on {calls * per_call} queries of the same workload "
+            f"(starts spread over the vertex range), {threads} threads, {dt:.1f} s")
+    return total_steps / dt, threads, desc
+
+
+def run_reference(args, w):
+    """--impl reference: the CPU oracle as the reference arm."""
+    rank, _, world = _dist_env()
+    if rank != 0:
+        return
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    g, _ = make_graph(w, dev)
+    g = g.to("cpu")
+    if dev == "cuda":
+        torch.cuda.empty_cache()
+    per_step = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, cores, desc = cpu_oracle_sample(g, w, seconds=per_step, seed=42 + i)
+        if i >= args.warmup:
+            vals.append(v)
+    value = sum(vals) / len(vals)
+    line = {
+        "impl": "reference", "metric": "walk steps/s", "value": value, "unit": "steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32 (exact-mode integer weights)", "data": "synthetic",
+        "config": {"workload": describe(w)},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _dist_env():
+    from paper_2404_08364_gb300.shard import env_rank
+    return env_rank()[0], env_rank()[1], env_rank()[2]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat25_node2vec", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch-log2", type=int, default=None)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    w = dict(WORKLOADS[args.workload])
+    if args.batch_log2 is not None:
+        w["batch_log2"] = args.batch_log2
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2404_08364_gb300.build import build
+    from paper_2404_08364_gb300.shard import reduce_scalar, shard_range
+
+    rank, local, world = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build()
+    from paper_2404_08364_gb300 import DeviceGraph
+
+    g, gen_s = make_graph(w, dev)
+    g_host = g.to("cpu") if (rank == 0 and world == 1 and not args.no_cpu) else None
+    # fast mode needs only FP32 weights on the device
+    keep_u32 = w["mode"] == "exact"
+    dg = DeviceGraph.from_tensors(g.row_ptr, g.col, g.w_f32, g.w_u32 if keep_u32 else None, g.etype,
+                                  borrow=True, device=dev)
+    graph_bytes = sum(t.numel() * t.element_size() for t in (g.row_ptr, g.col, g.w_f32))
+    batch = 2 ** w["batch_log2"]
+    # weak scaling: every rank runs `batch` queries per step, from its own shard
+    # of the query space (slices of one query per vertex)
+    stream = torch.cuda.current_stream(dev)
+    steps_total = args.warmup + args.steps
+    starts = []
+    for k in range(steps_total):
+        s = slice_starts(g.n, k, w["slices"], batch * world, dev)
+        b, e = shard_range(s.numel(), rank, world)
+        starts.append((s[b:e].contiguous(), (k % w["slices"]) * (g.n // w["slices"]) + b))
+    paths = torch.empty((batch, w["L"] + 1), dtype=torch.int32, device=dev)
+    plen = torch.empty(batch, dtype=torch.int32, device=dev)
+    kw = dict(mode=w["mode"], p=w["p"], q=w["q"], scale=2)
+
+    def step(k):
+        s, qid0 = starts[k]
+        dg.walk(w["algo"], s, w["L"], 42, q_id0=qid0, paths=paths[:s.numel()], path_len=plen[:s.numel()],
+                stream=stream, **kw)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    dg.stats_reset(stream)
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        step(args.warmup + i)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_each = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    ms_total = sum(ms_each)
+    st = dg.stats()
+    steps_local = st["steps"]
+    ms_max = reduce_scalar(ms_total, "max", dev)
+    steps_all = reduce_scalar(steps_local, "sum", dev)
+    value = steps_all / (ms_max / 1e3)
+
+    # end to end through the C ABI with pinned host buffers (rank-local)
+    e2e = None
+    if not args.no_e2e:
+        hs = [s.cpu().pin_memory() for s, _ in starts]
+        hp = torch.empty((batch, w["L"] + 1), dtype=torch.int32).pin_memory()
+        hl = torch.empty(batch, dtype=torch.int32).pin_memory()
+        dg.stats_reset(stream)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for i in range(args.steps):
+            k = args.warmup + i
+            n_q = hs[k].numel()
+            dg.walk(w["algo"], hs[k], w["L"], 42, q_id0=starts[k][1], paths=hp[:n_q], path_len=hl[:n_q],
+                    stream=stream, **kw)
+            h2d += n_q * 4
+            d2h += n_q * (w["L"] + 1) * 4 + n_q * 4
+        t1 = time.perf_counter()
+        e2e_steps = reduce_scalar(dg.stats()["steps"], "sum", dev)
+        e2e_s = reduce_scalar(t1 - t0, "max", dev)
+        e2e = {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d // args.steps,
+               "d2h_bytes_per_step": d2h // args.steps}
+
+    peak, peak_kind = load_peaks()
+    algo_bytes_per_launch = st["algo_bytes"] / args.steps
+    achieved = algo_bytes_per_launch / (ms_total / args.steps / 1e3) / 1e9
+    line = {
+        "metric": "walk steps/s", "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w["mode"] == "fast" else "u32",
+        "data": "synthetic",
+        "config": {"workload": describe(w), "graph": g.name, "n": g.n, "m": g.m,
+                   "graph_bytes_on_device": graph_bytes, "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"query shards x{world} (graph replicas)",
+                   "graph_gen_s": round(gen_s, 1), "tuning": dg.get_tuning()},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} (copy bandwidth)",
+                     "algo_bytes_per_launch": algo_bytes_per_launch,
+                     "kernel": "walk_kernel (persistent engine)"},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "e2e": e2e,
+        "counters": {k: st[k] for k in ("steps", "rows_scanned", "warp_steps", "block_steps", "n2v_tests")},
+    }
+    if g_host is not None:
+        del g
+        torch.cuda.empty_cache()
+        v, cores, desc = cpu_oracle_sample(g_host, w, seconds=args.cpu_seconds)
+        line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dg.free()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
