@@ -539,6 +539,9 @@ extern "C" int fw_stats(fw_graph* G, fw_stats_t* out) {
         if (cudaEventElapsedTime(&ms, G->ev0, G->ev1) == cudaSuccess) out->last_kernel_ms = ms;
         else cudaGetLastError();
     }
+    if (s.counters[C_TIMEOUT])
+        return fail(FW_ETIMEOUT, "fw_stats: a walk kernel stopped after a bounded wait ran out (%llu CTAs)",
+                    (unsigned long long)s.counters[C_TIMEOUT]);
     if (s.counters[C_BAD_INPUT])
         return fail(FW_EINVAL, "fw_stats: %llu queries had an out-of-range start/prev or negative step0 (written as empty paths)",
                     (unsigned long long)s.counters[C_BAD_INPUT]);

@@ -44,13 +44,14 @@ __host__ __device__ __forceinline__ uint4 step_block(uint64_t seed, uint64_t qid
                          make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
 }
 
-// Fast-mode reservoir draws: counter word 3 = 0x80000000 | lane << 20 | k, so
-// the streams of the (up to 1024) lanes of a sampler never meet each other or
+// Fast-mode reservoir draws: counter word 3 = 0x80000000 | lane << 16 | k.
+// `lane` numbers the sampler's lanes over all segments of a row (< 2^15), k
+// the lane's draws (< 2^16), so no two streams of one step meet each other or
 // the per-step block.
 __device__ __forceinline__ uint4 lane_block(uint64_t seed, uint64_t qid, uint32_t t, uint32_t lane,
                                             uint32_t k) {
     return philox4x32_10(make_uint4(t, (uint32_t)qid, (uint32_t)(qid >> 32),
-                                    0x80000000u | (lane << 20) | (k & 0xFFFFFu)),
+                                    0x80000000u | ((lane & 0x7FFFu) << 16) | (k & 0xFFFFu)),
                          make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
 }
 
@@ -98,6 +99,7 @@ enum CounterSlot {
     C_PROBES,
     C_ALGO_BYTES,
     C_BAD_INPUT,
+    C_TIMEOUT,
     C_NUM
 };
 

@@ -1,113 +1,63 @@
 // Persistent, degree-aware walk engine (FlowWalker Sections 4-5, re-designed
-// for sm_103a).
+// for sm_103a without block-wide barriers).
 //
-// One CTA is an independent worker with a local task pool of `slots` walks in
-// shared memory (Section 5.1's P_L).  Each iteration it
-//   1. claims new queries for its empty slots from one global atomic cursor
-//      (Section 5.2's global task pool P_G: the request arrays themselves,
-//      nothing extra in global memory),
-//   2. reads the row offsets of every active walk's current vertex and routes
-//      the step by degree: d <= d_warp to a warp sampler, larger rows to the
-//      CTA sampler (Section 5.1's two stages, d_t),
-//   3. runs the warp samplers concurrently, one step per small task,
-//   4. runs the CTA sampler on each large task in turn,
-//   5. commits each move to the caller's path row and retires finished walks.
-// A walk stays on its CTA for life; it moves between the warp and CTA
-// samplers from step to step as the degree of its current vertex changes.
+// Scheduling (Section 5's sampler-centric model and two-level task pools):
+//   * Every warp is an independent sampler with a few walk slots of its own
+//     in shared memory (its share of the CTA's local task pool P_L).  It
+//     claims queries from one global atomic cursor over the callers' request
+//     arrays (the global task pool P_G: nothing extra in global memory) and
+//     runs one step at a time on whichever of its walks is ready.
+//   * A step whose current row holds at most d_t entries is sampled by the
+//     warp alone (the warp sampler).  A longer row becomes a CTA hub task:
+//     it is cut into segments and every warp of the CTA that has a free
+//     moment takes segments through shared-memory atomics (the block
+//     sampler, without __syncthreads: warps join and leave freely).  The
+//     warp that finishes the last segment merges the result and commits the
+//     move; the walk then returns to its owner warp.  So a walk moves between
+//     the warp and the block sampler at every step, by the degree of the
+//     vertex it stands on, and never leaves its CTA.
 //
-// Samplers (Section 4's selection phase, no O(d) buffer in global memory):
+// Samplers (Section 4's selection phase; no O(d) buffer in global memory):
 //   exact mode: W = sum of integer weights, r = floor(x * W / 2^64) from the
 //     step's 64-bit Philox draw, pick = smallest i with inclusive prefix > r
-//     (inverse transform sampling done in two passes over the row, the first
-//     keeping per-segment sums in shared memory so the second re-reads one
-//     segment only);
-//   fast mode: a single pass of weighted reservoir sampling in its
-//     exponential-race form, each lane running Efraimidis-Spirakis reservoir
-//     sampling with exponential jumps over its share of the row (random draws
-//     only when the reservoir changes, O(log d) per lane) and the lanes'
-//     reservoirs merged by an arg-min over their race times.
+//     (inverse transform sampling, two passes: the first keeps one sum per
+//     128-entry chunk or per segment in shared memory, the second re-reads
+//     only the chunk or segment holding the crossing);
+//   fast mode: one pass of weighted reservoir sampling in exponential-race
+//     form: each lane runs Efraimidis-Spirakis reservoir sampling with
+//     exponential jumps over its entries (random draws only when its
+//     reservoir changes, O(log d) per lane), lanes and segments merged by an
+//     arg-min over race times (a 64-bit atomicMin of packed (time, index)
+//     across the warps of a hub task).
+//
+// Rows are streamed in 128-entry chunks (a lane holds one aligned quad of
+// four entries, 16-byte loads of columns and weights), with the next chunk's
+// loads in flight while the current one is sampled.
 #include <math.h>
+
+#include <type_traits>
 
 #include "fw_internal.cuh"
 
 namespace fw {
 namespace {
 
-constexpr int S_MAX = 128;   // slots per CTA, upper bound
-constexpr int SUBMAX = 32;   // exact CTA sampler: segment sums kept per warp
-constexpr int ST_EMPTY = 0, ST_ACTIVE = 1, ST_FINISH = 2;
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int INT_BIG = 0x7fffffff;
 constexpr int MODE_EXACT = 0, MODE_FAST = 1;
-
-template <int NT>
-struct __align__(16) Smem {
-    long long q[S_MAX];      // local query index inside its request
-    long long beg[S_MAX];    // row of cur
-    long long pbeg[S_MAX];   // row of prev (node2vec)
-    int req[S_MAX];
-    int cur[S_MAX], prev[S_MAX], t[S_MAX], lim[S_MAX], k[S_MAX];
-    int deg[S_MAX], pdeg[S_MAX];
-    int state[S_MAX];
-    int small_list[S_MAX], large_list[S_MAX], fin_list[S_MAX];
-    int warp_empty[S_MAX / 32];
-    int n_small, n_large, n_fin, n_active;
-    unsigned long long claim_base;
-    int claim_n, exhausted;
-    // CTA sampler scratch
-    unsigned long long red_sum[NT / 32];
-    unsigned long long sub_sum[NT / 32][SUBMAX];
-    float red_tau[NT / 32];
-    int red_idx[NT / 32];
-    int b_warp, b_sub, b_sel;
-    unsigned long long b_r;
-    unsigned int b_oz;
-    unsigned long long cnt[C_NUM];
-};
-
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long n = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += n;
-    }
-    return v;
-}
-
-// arg-min over (tau, idx), ties to the smaller index; idx < 0 means "none".
-__device__ __forceinline__ void warp_argmin(float& tau, int& idx) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        float t2 = __shfl_xor_sync(0xffffffffu, tau, o);
-        int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
-        bool take = (i2 >= 0) && (idx < 0 || t2 < tau || (t2 == tau && i2 < idx));
-        if (take) {
-            tau = t2;
-            idx = i2;
-        }
-    }
-}
-
-__device__ __forceinline__ float unit_open(uint32_t w) {
-    // (0, 1): 24 random bits, centred in their cell
-    return ((float)(w >> 8) + 0.5f) * (1.0f / 16777216.0f);
-}
-
-// Is u in the sorted row col[pb .. pb+pd)?  Plain binary search (v1).
-__device__ __forceinline__ bool in_row(const int32_t* __restrict__ col, long long pb, int pd, int u) {
-    int lo = 0, hi = pd;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        int v = __ldg(col + pb + mid);
-        if (v < u) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo < pd && __ldg(col + pb + lo) == u;
-}
+constexpr int WIN = 128;          // staged window of N(prev) per warp (node2vec)
+constexpr int SW_MAX = 8;         // walk slots per warp, upper bound
+constexpr int NHUB = 4;           // hub tasks open at once per CTA
+constexpr int NSEG_MAX = 64;      // segments per hub task
+constexpr int NCHUNK_MAX = 64;    // exact warp sampler: chunk sums (d_t <= 8192)
+constexpr int NST = 6;            // TMA ring stages per warp
+constexpr int CHQ = 32;           // quads per chunk (one per lane)
+constexpr int ST_COL = 0, ST_W = CHQ * 16, ST_ET = CHQ * 32;
+constexpr int STAGE_BYTES = CHQ * 36;  // columns, weights, labels of one chunk
+constexpr int ST_EMPTY = 0, ST_READY = 1, ST_HUB = 2, ST_FINISH = 3;
+// hub task control word: state << 24 | next segment to hand out
+constexpr int H_FREE = 0, H_SETUP = 1, H_ACTIVE = 2;
+constexpr unsigned H_SEG_MASK = 0xFFFFFFu;
 
 // Per-step view of one walk, held in registers by the lanes of its sampler.
 struct StepCtx {
@@ -118,448 +68,1043 @@ struct StepCtx {
     int prev;
     int algo;
     int want;   // MetaPath label for this move
-    uint32_t fi[3];
-    float ff[3];
+    uint32_t fi0, fi1, fi2;
+    float ff0, ff1, ff2;
 };
 
-__device__ __forceinline__ int n2v_class(const GraphDev& g, const StepCtx& c, int u) {
-    if (u == c.prev) return 0;
-    return in_row(g.col, c.pbeg, c.pdeg, u) ? 1 : 2;
+// A CTA hub task: one step of one walk whose row is longer than d_t.
+struct HubTask {
+    unsigned ctl;     // state << 24 | next_seg; one atomic both claims a
+                      // segment and tells whether the task was live
+    int slot;         // owner slot (warp * SW_MAX + j)
+    int nseg;
+    int seg_q;        // quads per segment
+    int done_seg;
+    unsigned long long best;  // fast: (race-time bits << 32) | row index
+    StepCtx c;
+    uint64_t seed;
+    uint64_t qid;
+    uint32_t t;
+    int req;
+    unsigned long long seg_sum[NSEG_MAX];  // exact
+};
+
+template <int NT>
+struct __align__(16) Smem {
+    static constexpr int NS = (NT / 32) * SW_MAX;
+    long long q[NS];      // local query index inside its request
+    long long pbeg[NS];   // row of prev (node2vec)
+    int req[NS];
+    int cur[NS], prev[NS], t[NS], lim[NS], k[NS], pdeg[NS];
+    int state[NS];
+    HubTask hub[NHUB];
+    int abort_flag;
+};
+
+// ------------------------------------------------------------ small helpers
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
 }
 
-__device__ __forceinline__ uint32_t weight_exact(const GraphDev& g, const StepCtx& c, int i) {
-    const long long e = c.beg + i;
-    uint32_t w = __ldg(g.w_u32 + e);
-    if (c.algo == FW_METAPATH) {
-        if (__ldg(g.etype + e) != c.want) w = 0;
-    } else if (c.algo == FW_NODE2VEC && c.prev >= 0) {
-        w *= c.fi[n2v_class(g, c, __ldg(g.col + e))];
+__device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long long v, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long n = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += n;
     }
-    return w;
+    return v;
 }
 
-__device__ __forceinline__ float weight_fast(const GraphDev& g, const StepCtx& c, int i) {
-    const long long e = c.beg + i;
-    float w = __ldg(g.w_f32 + e);
-    if (c.algo == FW_METAPATH) {
-        if (__ldg(g.etype + e) != c.want) w = 0.0f;
-    } else if (c.algo == FW_NODE2VEC && c.prev >= 0) {
-        w *= c.ff[n2v_class(g, c, __ldg(g.col + e))];
+// arg-min over (tau, idx), ties to the smaller index; idx < 0 means "none".
+__device__ __forceinline__ void warp_argmin(float& tau, int& idx) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float t2 = __shfl_xor_sync(FULL, tau, o);
+        const int i2 = __shfl_xor_sync(FULL, idx, o);
+        const bool take = (i2 >= 0) && (idx < 0 || t2 < tau || (t2 == tau && i2 < idx));
+        if (take) {
+            tau = t2;
+            idx = i2;
+        }
     }
-    return w;
 }
 
-// One lane's weighted reservoir (exponential race with exponential jumps).
-// tau = the lane's current minimum race time E_i / w_i (E_i ~ Exp(1)), sel its
-// element; X = remaining weight before the next element beats tau.  An
-// element with weight w beats the current minimum with probability
-// 1 - exp(-w * tau), so the weight skipped before the next record is
-// Exp(1) / tau; the record's own time is the race time conditioned on being
-// below tau.
-struct Reservoir {
+__device__ __forceinline__ float unit_open(uint32_t w) {
+    // strictly inside (0, 1): 23 random bits centred in their cell, so the
+    // largest value is 1 - 2^-24 (exact in FP32) and -log(u) > 0 always
+    return ((float)(w >> 9) + 0.5f) * (1.0f / 8388608.0f);
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // bounded waits: 2 s
+
+// ------------------------------------------------- TMA bulk copies, mbarriers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of an mbarrier; false after kWaitLimitNs (a copy
+// that never lands means a bug: the caller then stops cleanly).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_timer_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+// 1-D bulk copy global -> shared, completion counted in bytes on `bar`.
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// A warp's private ring of NST chunk buffers in shared memory, each with its
+// mbarrier and a flag telling whether the chunk came by TMA (0) or must be
+// read from global memory (1: it touches the unpadded end of the arrays).
+// `seq` counts the chunks the warp has ever issued: chunk seq lives in stage
+// seq % NST and completes phase (seq / NST) & 1 of that stage's barrier.
+struct WarpPipe {
+    unsigned char* buf;
+    unsigned long long* bar;
+    int* direct;
+    uint32_t seq;
+};
+
+// --------------------------------------------------------------------------
+// node2vec membership: is a neighbour u of cur also in N(prev)?  Both rows are
+// sorted, so the entries of one 128-entry chunk of N(cur) can only match the
+// contiguous window of N(prev) between the chunk's smallest and largest
+// value.  A warp keeps one cursor into N(prev) that only moves forward (the
+// chunks ascend), finds each window with ballots over coalesced 32-entry
+// blocks (a 32-ary search when it has to skip far), stages it in shared
+// memory and lets every lane search its own four entries there.  N(prev) is
+// read about once (its part that overlaps N(cur)), instead of a log2 d(prev)
+// probe chain per neighbour.
+// --------------------------------------------------------------------------
+
+// First index i >= pos with B[i] >= x, or pd.  Warp-collective, uniform result.
+__device__ __forceinline__ int lower_bound_from(const int32_t* __restrict__ B, int pd, int pos, int x, int lane) {
+    {
+        const int idx = pos + lane;
+        const int v = idx < pd ? __ldg(B + idx) : INT_BIG;
+        const unsigned m = __ballot_sync(FULL, v < x);
+        if (m != FULL) return pos + __popc(m);
+    }
+    int lo = pos + 32, hi = pd;  // the answer lies in [lo, hi]
+    while (hi - lo > 32) {
+        const int s = (hi - lo + 31) >> 5;
+        const long long idx = (long long)lo + (long long)s * (lane + 1) - 1;
+        const int v = idx < hi ? __ldg(B + idx) : INT_BIG;
+        const int k = __popc(__ballot_sync(FULL, v < x));
+        const int nlo = lo + s * k;
+        const long long nhi = (long long)lo + (long long)s * (k + 1) - 1;
+        lo = nlo;
+        hi = nhi < hi ? (int)nhi : hi;
+    }
+    const int v = lo + lane < hi ? __ldg(B + lo + lane) : INT_BIG;
+    return lo + __popc(__ballot_sync(FULL, v < x));
+}
+
+// Bit j of the result: entry j of this lane's quad (valid bit j) is in B.
+// Warp-collective; `pos` is the warp's forward cursor into B.
+__device__ __forceinline__ unsigned chunk_members(const int32_t* __restrict__ B, int pd, int& pos,
+                                                  const int (&c)[4], unsigned valid, int lane,
+                                                  int* __restrict__ win) {
+    int lmin = INT_BIG, lmax = -1;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        if (valid >> j & 1u) {
+            lmin = min(lmin, c[j]);
+            lmax = max(lmax, c[j]);
+        }
+    const int amin = __reduce_min_sync(FULL, lmin);
+    const int amax = __reduce_max_sync(FULL, lmax);
+    if (amin == INT_BIG || pos >= pd) return 0u;
+    const int lo = lower_bound_from(B, pd, pos, amin, lane);
+    int hi = lo;
+    bool big = false;
+    for (;;) {
+        const int idx = hi + lane;
+        const int v = idx < pd ? __ldg(B + idx) : INT_BIG;
+        const int k = __popc(__ballot_sync(FULL, v <= amax));
+        if (hi - lo + k <= WIN) {
+            if (lane < k) win[hi - lo + lane] = v;
+        } else {
+            big = true;
+        }
+        hi += k;
+        if (k < 32) break;
+        if (big) {
+            hi = lower_bound_from(B, pd, hi, amax + 1, lane);
+            break;
+        }
+    }
+    pos = hi;
+    const int len = hi - lo;
+    if (len == 0) return 0u;
+    __syncwarp();
+    unsigned flags = 0;
+    if (!big) {
+        int from = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!(valid >> j & 1u)) continue;
+            int a = from, b = len;
+            while (a < b) {
+                const int mid = (a + b) >> 1;
+                if (win[mid] < c[j]) a = mid + 1;
+                else b = mid;
+            }
+            if (a < len && win[a] == c[j]) flags |= 1u << j;
+            from = a;
+        }
+    } else {
+        int from = lo;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (!(valid >> j & 1u)) continue;
+            int a = from, b = hi;
+            while (a < b) {
+                const int mid = (a + b) >> 1;
+                if (__ldg(B + mid) < c[j]) a = mid + 1;
+                else b = mid;
+            }
+            if (a < hi && __ldg(B + a) == c[j]) flags |= 1u << j;
+            from = a;
+        }
+    }
+    __syncwarp();  // the window is rewritten by the next chunk
+    return flags;
+}
+
+// One lane's four consecutive row entries (an aligned quad of the CSR
+// arrays) with the state-dependent weight of each (0 outside the row).
+template <int MODE>
+struct Quad {
+    typedef typename std::conditional<MODE == MODE_EXACT, uint32_t, float>::type W;
+    int c[4];
+    W w[4];
+    unsigned valid;
+};
+
+template <int MODE>
+__device__ __forceinline__ void clear_quad(Quad<MODE>& Q) {
+    Q.valid = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        Q.c[j] = INT_BIG;
+        Q.w[j] = 0;
+    }
+}
+
+// Load quad q of the row [beg, end) and apply the weight rule except the
+// node2vec factor (which needs the warp-collective membership test).
+template <int MODE>
+__device__ __forceinline__ void load_quad(const GraphDev& g, const StepCtx& cx, long long q, long long end,
+                                          Quad<MODE>& Q) {
+    const long long e0 = q << 2;
+    clear_quad(Q);
+    int et = 0;
+    if (e0 + 3 < g.m) {
+        const int4 cv = __ldg(reinterpret_cast<const int4*>(g.col + e0));
+        Q.c[0] = cv.x; Q.c[1] = cv.y; Q.c[2] = cv.z; Q.c[3] = cv.w;
+        if (MODE == MODE_EXACT) {
+            const uint4 wv = __ldg(reinterpret_cast<const uint4*>(g.w_u32 + e0));
+            Q.w[0] = wv.x; Q.w[1] = wv.y; Q.w[2] = wv.z; Q.w[3] = wv.w;
+        } else {
+            const float4 wv = __ldg(reinterpret_cast<const float4*>(g.w_f32 + e0));
+            Q.w[0] = wv.x; Q.w[1] = wv.y; Q.w[2] = wv.z; Q.w[3] = wv.w;
+        }
+        if (cx.algo == FW_METAPATH) et = __ldg(reinterpret_cast<const int*>(g.etype + e0));
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const long long e = e0 + j;
+            if (e < g.m) {
+                Q.c[j] = __ldg(g.col + e);
+                if (MODE == MODE_EXACT) Q.w[j] = __ldg(g.w_u32 + e);
+                else Q.w[j] = __ldg(g.w_f32 + e);
+                if (cx.algo == FW_METAPATH) et |= ((int)(uint8_t)__ldg(g.etype + e)) << (8 * j);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const long long e = e0 + j;
+        if (e >= cx.beg && e < end) {
+            Q.valid |= 1u << j;
+            if (cx.algo == FW_METAPATH && (int)(int8_t)(et >> (8 * j)) != cx.want) Q.w[j] = 0;
+        } else {
+            Q.c[j] = INT_BIG;
+            Q.w[j] = 0;
+        }
+    }
+}
+
+// Apply the node2vec factors to a loaded quad (warp-collective: every lane
+// of the warp must call it).
+template <int MODE>
+__device__ __forceinline__ void n2v_apply(const GraphDev& g, const StepCtx& cx, Quad<MODE>& Q, int& pos, int lane,
+                                          int* win) {
+    if (cx.algo != FW_NODE2VEC || cx.prev < 0) return;
+    const unsigned mem = chunk_members(g.col + cx.pbeg, cx.pdeg, pos, Q.c, Q.valid, lane, win);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const bool isprev = Q.c[j] == cx.prev;
+        const bool in = mem >> j & 1u;
+        if (MODE == MODE_EXACT) Q.w[j] *= isprev ? cx.fi0 : (in ? cx.fi1 : cx.fi2);
+        else Q.w[j] *= isprev ? cx.ff0 : (in ? cx.ff1 : cx.ff2);
+    }
+}
+
+// A warp's weighted reservoir (exponential race with exponential jumps),
+// run over the warp's entries in row order, 128 at a time.  tau = the current
+// minimum race time E_i / w_i (E_i ~ Exp(1)) and sel its entry; X = the
+// weight still to pass before some entry beats tau.  An entry of weight w
+// beats the minimum with probability 1 - exp(-w tau), so the weight skipped
+// before the next record is Exp(1) / tau; the record's own time is the race
+// time conditioned to lie below tau.  Every lane holds the same state: a
+// chunk costs one warp prefix sum and one comparison unless a record falls
+// inside it, and a row of d entries makes about ln d records.  X is kept in
+// double so that subtracting many chunk totals does not drift.
+struct WarpRes {
     float tau;
-    float X;
     int sel;
+    double X;
     uint32_t ctr;
     uint32_t spare0, spare1;
-    bool has_spare;
+    uint32_t has_spare;
 
     __device__ __forceinline__ void init() {
         tau = __int_as_float(0x7f800000);  // +inf
-        X = 0.0f;
         sel = -1;
+        X = 0.0;
         ctr = 0;
-        has_spare = false;
-    }
-
-    __device__ __forceinline__ void offer(int i, float w, uint64_t seed, uint64_t qid, uint32_t t,
-                                          uint32_t lane) {
-        if (!(w > 0.0f)) return;
-        X -= w;
-        if (X > 0.0f) return;
-        uint32_t a, b;
-        if (has_spare) {
-            a = spare0;
-            b = spare1;
-            has_spare = false;
-        } else {
-            uint4 o = lane_block(seed, qid, t, lane, ctr++);
-            a = o.x;
-            b = o.y;
-            spare0 = o.z;
-            spare1 = o.w;
-            has_spare = true;
-        }
-        const float u1 = unit_open(a), u2 = unit_open(b);
-        float e;
-        if (isinf(tau)) e = -logf(u1);
-        else e = -log1pf(u1 * expm1f(-w * tau));
-        tau = e / w;
-        sel = i;
-        X = -logf(u2) / tau;
+        has_spare = 0;
     }
 };
 
-template <int NT>
-__device__ __forceinline__ void count_step(Smem<NT>& sm, int d, int algo, bool warp_tier) {
-    atomicAdd(&sm.cnt[C_STEPS], 1ull);
-    atomicAdd(&sm.cnt[C_ROWS], (unsigned long long)d);
-    atomicAdd(&sm.cnt[warp_tier ? C_WARP_STEPS : C_BLOCK_STEPS], 1ull);
-    if (algo == FW_NODE2VEC) atomicAdd(&sm.cnt[C_PROBES], (unsigned long long)d);
-    atomicAdd(&sm.cnt[C_ALGO_BYTES],
-              (unsigned long long)(8ll * d + (algo == FW_METAPATH ? d : 0) + 16 + 4));
+// A new record at row entry idx of weight w (uniform across the warp).
+__device__ __noinline__ WarpRes warp_record(WarpRes r, int idx, float w, uint64_t seed, uint64_t qid, uint32_t t,
+                                            uint32_t stream) {
+    uint32_t a, b;
+    if (r.has_spare) {
+        a = r.spare0;
+        b = r.spare1;
+        r.has_spare = 0;
+    } else {
+        const uint4 o = lane_block(seed, qid, t, stream, r.ctr++);
+        a = o.x;
+        b = o.y;
+        r.spare0 = o.z;
+        r.spare1 = o.w;
+        r.has_spare = 1;
+    }
+    const float u1 = unit_open(a), u2 = unit_open(b);
+    float e;
+    if (isinf(r.tau)) e = -logf(u1);
+    else e = -log1pf(u1 * expm1f(-w * r.tau));
+    r.tau = e / w;
+    r.sel = idx;
+    r.X = (double)(-logf(u2)) / (double)r.tau;
+    return r;
 }
 
-// Commit a move (one thread): append `next` to the path, advance the state,
-// apply the PPR stop test and the length limit.
-template <int NT>
-__device__ __forceinline__ void commit(Smem<NT>& sm, const ReqDev& R, int s, int next, uint32_t oz) {
-    const long long width = (long long)R.max_len + 1;
-    const int k = sm.k[s];
-    R.paths[sm.q[s] * width + k] = next;
-    sm.k[s] = k + 1;
-    sm.prev[s] = sm.cur[s];
-    sm.pbeg[s] = sm.beg[s];
-    sm.pdeg[s] = sm.deg[s];
-    sm.cur[s] = next;
-    const int t = sm.t[s] + 1;
-    sm.t[s] = t;
-    const bool stop = (R.algo == FW_PPR && oz < R.t_stop) || t >= sm.lim[s];
-    if (stop) sm.state[s] = ST_FINISH;
-}
-
-template <int NT>
-__device__ __forceinline__ StepCtx make_ctx(const Smem<NT>& sm, const ReqDev& R, int s) {
-    StepCtx c;
-    c.beg = sm.beg[s];
-    c.d = sm.deg[s];
-    c.pbeg = sm.pbeg[s];
-    c.pdeg = sm.pdeg[s];
-    c.prev = sm.prev[s];
-    c.algo = R.algo;
-    c.want = (R.algo == FW_METAPATH) ? (int)R.schema[sm.t[s] % R.schema_len] : -1;
+// Offer one chunk: lane `lane` holds entries e0 .. e0+3 (row indices) with
+// weights w[0..3]; entries are visited in lane order, then j.
+__device__ __forceinline__ void warp_offer_chunk(WarpRes& R, const float (&w)[4], int e0, int lane, uint64_t seed,
+                                                 uint64_t qid, uint32_t t, uint32_t stream) {
+    const float l0 = w[0], l1 = l0 + w[1], l2 = l1 + w[2], l3 = l2 + w[3];
+    float incl = l3;
 #pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        c.fi[j] = R.fac_i[j];
-        c.ff[j] = R.fac_f[j];
+    for (int o = 1; o < 32; o <<= 1) {
+        const float n = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += n;
     }
-    return c;
+    const float tot = __shfl_sync(FULL, incl, 31);
+    if (R.X > (double)tot) {  // no record in this chunk (the common case)
+        R.X -= (double)tot;
+        return;
+    }
+    const float excl = incl - l3;
+    const float cum[4] = {excl + l0, excl + l1, excl + l2, excl + l3};
+    double target = R.X;  // a record falls on the first entry whose cumulative weight reaches target
+    int last = -1;        // chunk position (lane * 4 + j) of the last record: each record lies beyond it
+    for (;;) {
+        int jj = -1;
+#pragma unroll
+        for (int j = 3; j >= 0; --j)
+            if (lane * 4 + j > last && w[j] > 0.0f && (double)cum[j] >= target) jj = j;
+        const unsigned m = __ballot_sync(FULL, jj >= 0);
+        if (!m) {
+            R.X = target - (double)tot;
+            return;
+        }
+        const int L = __ffs(m) - 1;
+        float wj = 0.0f, cj = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j == jj) {
+                wj = w[j];
+                cj = cum[j];
+            }
+        const float wr = __shfl_sync(FULL, wj, L);
+        const float cr = __shfl_sync(FULL, cj, L);
+        const int idx = __shfl_sync(FULL, e0 + jj, L);
+        last = L * 4 + __shfl_sync(FULL, jj, L);
+        R = warp_record(R, idx, wr, seed, qid, t, stream);
+        target = (double)cr + R.X;
+    }
 }
 
-// ----------------------------------------------------------- warp samplers
-
-template <int MODE, int NT>
-__device__ void warp_step(const GraphDev& g, const ReqDev* __restrict__ reqs, Smem<NT>& sm, int s,
-                          uint32_t* __restrict__ wbuf, int lane) {
-    const ReqDev& R = reqs[sm.req[s]];
-    const StepCtx c = make_ctx(sm, R, s);
-    const uint32_t t = (uint32_t)sm.t[s];
-    const uint64_t qid = (uint64_t)(R.q_id0 + sm.q[s]);
-    int sel = -1;
-    uint32_t oz = 0xFFFFFFFFu;
-    if (MODE == MODE_EXACT) {
-        unsigned long long sum = 0;
-        for (int i = lane; i < c.d; i += 32) {
-            const uint32_t w = weight_exact(g, c, i);
-            wbuf[i] = w;
-            sum += w;
-        }
-        const unsigned long long W = warp_sum_u64(sum);
-        __syncwarp();
-        if (W != 0) {
-            const uint4 o = step_block(R.seed, qid, t);
-            oz = o.z;
-            const unsigned long long x = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
-            const unsigned long long r = __umul64hi(x, W);
-            unsigned long long run = 0;
-            for (int base = 0; base < c.d; base += 32) {
-                const int i = base + lane;
-                const unsigned long long v = (i < c.d) ? wbuf[i] : 0ull;
-                const unsigned long long incl = warp_incl_scan_u64(v, lane);
-                const unsigned m = __ballot_sync(0xffffffffu, run + incl > r);
-                if (m) {
-                    sel = base + __ffs(m) - 1;
-                    break;
-                }
-                run += __shfl_sync(0xffffffffu, incl, 31);
-            }
-        }
-    } else {
-        Reservoir res;
-        res.init();
-        for (int i = lane; i < c.d; i += 32) res.offer(i, weight_fast(g, c, i), R.seed, qid, t, lane);
-        float tau = res.tau;
-        int idx = res.sel;
-        warp_argmin(tau, idx);
-        sel = idx;
-        if (sel >= 0 && R.algo == FW_PPR) oz = step_block(R.seed, qid, t).z;
+// Pick inside one lane's quad: smallest j whose prefix exceeds rr.
+__device__ __forceinline__ int pick_in_quad(const uint32_t (&w)[4], unsigned long long rr) {
+    unsigned long long acc = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        acc += w[j];
+        if (acc > rr) return j;
     }
-    if (lane == 0) {
-        if (sel < 0) {
-            sm.state[s] = ST_FINISH;  // nothing selectable: the walk stops here
-        } else {
-            count_step(sm, c.d, c.algo, true);
-            commit(sm, R, s, __ldg(g.col + c.beg + sel), oz);
-        }
-    }
-    __syncwarp();
+    return 3;
 }
 
-// ------------------------------------------------------------ CTA sampler
-
-template <int MODE, int NT>
-__device__ void block_step(const GraphDev& g, const ReqDev* __restrict__ reqs, Smem<NT>& sm, int s) {
-    constexpr int NW = NT / 32;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const ReqDev& R = reqs[sm.req[s]];
-    const StepCtx c = make_ctx(sm, R, s);
-    const uint32_t t = (uint32_t)sm.t[s];
-    const uint64_t qid = (uint64_t)(R.q_id0 + sm.q[s]);
-    // warp w owns the contiguous segment [w0, w1) of the row
-    const int seg = ((c.d + NW - 1) / NW + 31) & ~31;
-    const int w0 = min(c.d, warp * seg), w1 = min(c.d, w0 + seg);
-
-    if (MODE == MODE_EXACT) {
-        int sub = (seg + SUBMAX - 1) / SUBMAX;
-        sub = max(256, (sub + 31) & ~31);
-        unsigned long long total = 0;
-        int j = 0;
-        for (int a = w0; a < w1; a += sub, ++j) {
-            const int b = min(w1, a + sub);
-            unsigned long long sum = 0;
-            for (int i = a + lane; i < b; i += 32) sum += weight_exact(g, c, i);
-            sum = warp_sum_u64(sum);
-            if (lane == 0) sm.sub_sum[warp][j] = sum;
-            total += sum;
-        }
-        if (lane == 0) sm.red_sum[warp] = total;
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long W = 0;
-            for (int w = 0; w < NW; ++w) W += sm.red_sum[w];
-            sm.b_warp = -1;
-            sm.b_sel = -1;
-            if (W != 0) {
-                const uint4 o = step_block(R.seed, qid, t);
-                sm.b_oz = o.z;
-                const unsigned long long x = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
-                unsigned long long r = __umul64hi(x, W);
-                // r < W, so both searches stop inside the arrays; the bounds
-                // only guard against a logic error
-                int w = 0;
-                while (w < NW - 1 && r >= sm.red_sum[w]) r -= sm.red_sum[w++];
-                const int ws0 = min(c.d, w * seg);
-                const int nsub = (min(c.d, ws0 + seg) - ws0 + sub - 1) / sub;
-                int jj = 0;
-                while (jj < nsub - 1 && r >= sm.sub_sum[w][jj]) r -= sm.sub_sum[w][jj++];
-                sm.b_warp = w;
-                sm.b_sub = ws0 + jj * sub;  // first element of the segment
-                sm.b_r = r;
-            }
-        }
-        __syncthreads();
-        if (warp == sm.b_warp) {
-            const int a = sm.b_sub;
-            const int b = min(min(c.d, warp * seg + seg), a + sub);
-            const unsigned long long r = sm.b_r;
-            unsigned long long run = 0;
-            for (int base = a; base < b; base += 32) {
-                const int i = base + lane;
-                const unsigned long long v = (i < b) ? weight_exact(g, c, i) : 0ull;
-                const unsigned long long incl = warp_incl_scan_u64(v, lane);
-                const unsigned m = __ballot_sync(0xffffffffu, run + incl > r);
-                if (m) {
-                    if (lane == 0) sm.b_sel = base + __ffs(m) - 1;
-                    break;
-                }
-                run += __shfl_sync(0xffffffffu, incl, 31);
-            }
-        }
-        __syncthreads();
+// Lane 0: start loading chunk number `seq` (quads [qs, qs + nq), qs a
+// multiple of 4) into its stage of the warp's ring.
+template <int MODE>
+__device__ __forceinline__ void pipe_issue(const GraphDev& g, WarpPipe& P, uint32_t seq, long long qs, int nq,
+                                           bool labels) {
+    const int st = seq % NST;
+    unsigned char* b = P.buf + st * STAGE_BYTES;
+    const long long nq4 = (nq + 3) & ~3;
+    if (4 * (qs + nq4) <= g.m) {
+        P.direct[st] = 0;
+        const uint32_t bytes = (uint32_t)(nq4 * 32 + (labels ? nq4 * 4 : 0));
+        mbar_arrive_expect_tx(&P.bar[st], bytes);
+        tma_load_1d(b + ST_COL, g.col + 4 * qs, (uint32_t)(nq4 * 16), &P.bar[st]);
+        if (MODE == MODE_EXACT) tma_load_1d(b + ST_W, g.w_u32 + 4 * qs, (uint32_t)(nq4 * 16), &P.bar[st]);
+        else tma_load_1d(b + ST_W, g.w_f32 + 4 * qs, (uint32_t)(nq4 * 16), &P.bar[st]);
+        if (labels) tma_load_1d(b + ST_ET, g.etype + 4 * qs, (uint32_t)(nq4 * 4), &P.bar[st]);
     } else {
-        Reservoir res;
-        res.init();
-        for (int i = w0 + lane; i < w1; i += 32) res.offer(i, weight_fast(g, c, i), R.seed, qid, t, tid);
-        float tau = res.tau;
-        int idx = res.sel;
-        warp_argmin(tau, idx);
-        if (lane == 0) {
-            sm.red_tau[warp] = tau;
-            sm.red_idx[warp] = idx;
+        P.direct[st] = 1;
+        mbar_arrive(&P.bar[st]);
+    }
+}
+
+// Quad `lane` of a landed chunk (quads [qs, qs + 32)), masked to quads below
+// qb and entries inside the row [c.beg, end), MetaPath label applied.
+template <int MODE>
+__device__ __forceinline__ void stage_quad(const GraphDev& g, const StepCtx& c, const WarpPipe& P, int st,
+                                           long long qs, long long qb, long long end, int lane, Quad<MODE>& Q) {
+    const long long q = qs + lane;
+    if (q >= qb) {
+        clear_quad(Q);
+        return;
+    }
+    if (P.direct[st]) {
+        load_quad<MODE>(g, c, q, end, Q);
+        return;
+    }
+    const unsigned char* b = P.buf + st * STAGE_BYTES;
+    const int4 cv = *reinterpret_cast<const int4*>(b + ST_COL + lane * 16);
+    Q.c[0] = cv.x; Q.c[1] = cv.y; Q.c[2] = cv.z; Q.c[3] = cv.w;
+    if (MODE == MODE_EXACT) {
+        const uint4 wv = *reinterpret_cast<const uint4*>(b + ST_W + lane * 16);
+        Q.w[0] = wv.x; Q.w[1] = wv.y; Q.w[2] = wv.z; Q.w[3] = wv.w;
+    } else {
+        const float4 wv = *reinterpret_cast<const float4*>(b + ST_W + lane * 16);
+        Q.w[0] = wv.x; Q.w[1] = wv.y; Q.w[2] = wv.z; Q.w[3] = wv.w;
+    }
+    const int et = c.algo == FW_METAPATH ? *reinterpret_cast<const int*>(b + ST_ET + lane * 4) : 0;
+    Q.valid = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const long long e = (q << 2) + j;
+        if (e >= c.beg && e < end) {
+            Q.valid |= 1u << j;
+            if (c.algo == FW_METAPATH && (int)(int8_t)(et >> (8 * j)) != c.want) Q.w[j] = 0;
+        } else {
+            Q.c[j] = INT_BIG;
+            Q.w[j] = 0;
         }
-        __syncthreads();
-        if (warp == 0) {
-            float tt = lane < NW ? sm.red_tau[lane] : __int_as_float(0x7f800000);
-            int ii = lane < NW ? sm.red_idx[lane] : -1;
-            warp_argmin(tt, ii);
-            if (lane == 0) {
-                sm.b_sel = ii;
-                sm.b_oz = (ii >= 0 && R.algo == FW_PPR) ? step_block(R.seed, qid, t).z : 0xFFFFFFFFu;
+    }
+}
+
+// Stream quads [qa, qb) (qa a multiple of 4) of the row [c.beg, end) through
+// the warp's TMA ring, NST - 1 chunks ahead: weights with the node2vec
+// factors applied, then (fast) the warp's reservoir drawing from random
+// stream rng_stream, or (exact) each lane's running sum and, if chunk_sums
+// is given, one warp total per chunk.  False if a copy never landed.
+template <int MODE>
+__device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, long long qa, long long qb,
+                                           long long end, int lane, int* __restrict__ win, WarpPipe& P,
+                                           WarpRes& res, unsigned long long& lane_sum,
+                                           unsigned long long* __restrict__ chunk_sums, uint32_t rng_stream,
+                                           uint64_t seed, uint64_t qid, uint32_t t) {
+    const int nch = (int)((qb - qa + CHQ - 1) / CHQ);
+    const bool labels = c.algo == FW_METAPATH;
+    if (lane == 0)
+        for (int k = 0; k < nch && k < NST; ++k)
+            pipe_issue<MODE>(g, P, P.seq + k, qa + (long long)k * CHQ, (int)min((long long)CHQ, qb - qa - (long long)k * CHQ), labels);
+    int pos = 0;
+    bool ok = true;
+    for (int k = 0; k < nch; ++k) {
+        const uint32_t sq = P.seq + k;
+        const int st = sq % NST;
+        const long long qs = qa + (long long)k * CHQ;
+        if (!mbar_wait_bounded(&P.bar[st], (sq / NST) & 1u)) ok = false;
+        if (!__all_sync(FULL, ok)) {
+            ok = false;
+            // let the copies already issued land before giving up
+            if (lane == 0)
+                for (int kk = k + 1; kk < nch && kk < k + NST; ++kk)
+                    mbar_wait_bounded(&P.bar[(P.seq + kk) % NST], ((P.seq + kk) / NST) & 1u);
+            P.seq += min(nch, k + NST);
+            return false;
+        }
+        Quad<MODE> cur;
+        stage_quad<MODE>(g, c, P, st, qs, qb, end, lane, cur);
+        __syncwarp();  // every lane has its quad: the stage may be refilled
+        if (lane == 0 && k + NST < nch) {
+            const long long qn = qa + (long long)(k + NST) * CHQ;
+            pipe_issue<MODE>(g, P, sq + NST, qn, (int)min((long long)CHQ, qb - qn), labels);
+        }
+        n2v_apply<MODE>(g, c, cur, pos, lane, win);
+        if (MODE == MODE_FAST) {
+            const float wf[4] = {(float)cur.w[0], (float)cur.w[1], (float)cur.w[2], (float)cur.w[3]};
+            warp_offer_chunk(res, wf, (int)(((qs + lane) << 2) - c.beg), lane, seed, qid, t, rng_stream);
+        } else {
+            const unsigned long long s4 = (unsigned long long)cur.w[0] + cur.w[1] + cur.w[2] + cur.w[3];
+            lane_sum += s4;
+            if (chunk_sums) {
+                const unsigned long long cs = warp_sum_u64(s4);
+                if (lane == 0 && k < NCHUNK_MAX) chunk_sums[k] = cs;
             }
         }
-        __syncthreads();
     }
-    if (tid == 0) {
-        const int sel = sm.b_sel;
-        if (sel < 0) {
-            sm.state[s] = ST_FINISH;
-        } else {
-            count_step(sm, c.d, c.algo, false);
-            commit(sm, R, s, __ldg(g.col + c.beg + sel), sm.b_oz);
+    P.seq += nch;
+    return ok;
+}
+
+// Exact mode: scan quads [qa, qb) chunk by chunk and return the row-relative
+// index of the entry where the running prefix (from 0) first exceeds r.
+// Warp-collective, uniform result; -1 if the range sums to at most r.
+__device__ int exact_find(const GraphDev& g, const StepCtx& cx, long long qa, long long qb, long long end,
+                          unsigned long long r, int lane, int* win) {
+    int pos = 0;
+    unsigned long long run = 0;
+    for (long long qc = qa; qc < qb; qc += 32) {
+        const long long q = qc + lane;
+        Quad<MODE_EXACT> Q;
+        if (q < qb) load_quad<MODE_EXACT>(g, cx, q, end, Q);
+        else clear_quad(Q);
+        n2v_apply<MODE_EXACT>(g, cx, Q, pos, lane, win);
+        const unsigned long long s = (unsigned long long)Q.w[0] + Q.w[1] + Q.w[2] + Q.w[3];
+        const unsigned long long incl = warp_incl_scan_u64(s, lane);
+        const unsigned m = __ballot_sync(FULL, run + incl > r);
+        if (m) {
+            const int L = __ffs(m) - 1;
+            int sel = 0;
+            if (lane == L) sel = (int)((q << 2) + pick_in_quad(Q.w, r - (run + incl - s)) - cx.beg);
+            return __shfl_sync(FULL, sel, L);
         }
+        run += __shfl_sync(FULL, incl, 31);
     }
-    __syncthreads();
+    return -1;
+}
+
+// Find which of the n sums (n <= 64) holds the crossing of r, and r's offset
+// inside it.  Warp-collective; sums lives in shared memory.
+__device__ __forceinline__ int find_crossing(const unsigned long long* sums, int n, unsigned long long& r, int lane) {
+    unsigned long long run = 0;
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const unsigned long long v = i < n ? sums[i] : 0ull;
+        const unsigned long long incl = warp_incl_scan_u64(v, lane);
+        const unsigned m = __ballot_sync(FULL, run + incl > r);
+        if (m) {
+            const int L = __ffs(m) - 1;
+            const unsigned long long before = __shfl_sync(FULL, run + incl - v, L);
+            r -= before;
+            return base + L;
+        }
+        run += __shfl_sync(FULL, incl, 31);
+    }
+    return -1;
 }
 
 __device__ __forceinline__ int find_req(const ReqDev* __restrict__ reqs, int n_req, long long gq) {
     int lo = 0, hi = n_req - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(&reqs[mid].q_begin) <= gq) lo = mid;
+        if (reqs[mid].q_begin <= gq) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
+// Per-warp counters, kept by lane 0 and flushed at exit.
+struct Counters {
+    unsigned long long v[C_NUM];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int i = 0; i < C_NUM; ++i) v[i] = 0;
+    }
+    __device__ __forceinline__ void step(int d, int algo, bool hub) {
+        v[C_STEPS] += 1;
+        v[C_ROWS] += (unsigned long long)d;
+        v[hub ? C_BLOCK_STEPS : C_WARP_STEPS] += 1;
+        if (algo == FW_NODE2VEC) v[C_PROBES] += (unsigned long long)d;
+        v[C_ALGO_BYTES] += (unsigned long long)(8ll * d + (algo == FW_METAPATH ? d : 0) + 16 + 4);
+    }
+};
+
+template <int NT>
+__device__ __forceinline__ StepCtx make_ctx(const Smem<NT>& sm, const ReqDev& R, int s, long long beg, int d) {
+    StepCtx c;
+    c.beg = beg;
+    c.d = d;
+    c.pbeg = sm.pbeg[s];
+    c.pdeg = sm.pdeg[s];
+    c.prev = sm.prev[s];
+    c.algo = R.algo;
+    c.want = (R.algo == FW_METAPATH) ? (int)R.schema[sm.t[s] % R.schema_len] : -1;
+    c.fi0 = R.fac_i[0];
+    c.fi1 = R.fac_i[1];
+    c.fi2 = R.fac_i[2];
+    c.ff0 = R.fac_f[0];
+    c.ff1 = R.fac_f[1];
+    c.ff2 = R.fac_f[2];
+    return c;
+}
+
+// Commit a move of slot s (one thread): append `next` to the path, advance
+// the walk, apply the PPR stop test and the length limit, start fetching the
+// next row's offsets into L2, and hand the slot back (READY or FINISH).
+template <int NT>
+__device__ __forceinline__ void commit(const GraphDev& g, Smem<NT>& sm, const ReqDev& R, int s, const StepCtx& c,
+                                       int next, uint32_t oz) {
+    const long long width = (long long)R.max_len + 1;
+    const int k = sm.k[s];
+    R.paths[sm.q[s] * width + k] = next;
+    sm.k[s] = k + 1;
+    sm.prev[s] = sm.cur[s];
+    sm.pbeg[s] = c.beg;
+    sm.pdeg[s] = c.d;
+    sm.cur[s] = next;
+    const int t = sm.t[s] + 1;
+    sm.t[s] = t;
+    const bool stop = (R.algo == FW_PPR && oz < R.t_stop) || t >= sm.lim[s];
+    if (!stop) asm volatile("prefetch.global.L2 [%0];" ::"l"(g.row_ptr + next));
+    __threadfence_block();
+    *(volatile int*)&sm.state[s] = stop ? ST_FINISH : ST_READY;
+}
+
+// Finish the step of a hub task (the warp that completed its last segment).
+template <int MODE, int NT>
+__device__ void hub_finalize(const GraphDev& g, const ReqDev* __restrict__ reqs, Smem<NT>& sm, HubTask& H, int lane,
+                             int* win, Counters& cnt) {
+    const ReqDev& R = reqs[H.req];
+    const StepCtx c = H.c;
+    int sel = -1;
+    uint32_t oz = 0xFFFFFFFFu;
+    if (MODE == MODE_FAST) {
+        const unsigned long long b = H.best;
+        sel = b == ~0ull ? -1 : (int)(b & 0xFFFFFFFFull);
+        if (sel >= 0 && R.algo == FW_PPR) oz = step_block(H.seed, H.qid, H.t).z;
+    } else {
+        unsigned long long W = 0;
+        for (int j = lane; j < H.nseg; j += 32) W += H.seg_sum[j];
+        W = warp_sum_u64(W);
+        if (W != 0) {
+            const uint4 o = step_block(H.seed, H.qid, H.t);
+            oz = o.z;
+            const unsigned long long x = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+            unsigned long long r = __umul64hi(x, W);
+            const int j = find_crossing(H.seg_sum, H.nseg, r, lane);
+            if (j >= 0) {
+                const long long Q0a = (c.beg >> 2) & ~3ll, Q1 = (c.beg + c.d + 3) >> 2;
+                const long long qa = Q0a + (long long)j * H.seg_q;
+                sel = exact_find(g, c, qa, min(Q1, qa + H.seg_q), c.beg + c.d, r, lane, win);
+            }
+        }
+    }
+    if (lane == 0) {
+        const int s = H.slot;
+        if (sel < 0) {
+            __threadfence_block();
+            *(volatile int*)&sm.state[s] = ST_FINISH;
+        } else {
+            cnt.step(c.d, c.algo, true);
+            commit(g, sm, R, s, c, __ldg(g.col + c.beg + sel), oz);
+        }
+        __threadfence_block();
+        atomicExch(&H.ctl, (unsigned)H_FREE << 24);
+    }
+    __syncwarp();
+}
+
+// Take one segment of an open hub task, if any, and sample it.  Returns 1 if
+// the warp did hub work, 0 if none was open, -1 if a copy never landed.
+// Warp-collective.
+template <int MODE, int NT>
+__device__ int hub_help(const GraphDev& g, const ReqDev* __restrict__ reqs, Smem<NT>& sm, int lane, int* win,
+                        WarpPipe& P, Counters& cnt) {
+    int h = -1, j = -1;
+    if (lane == 0) {
+        for (int i = 0; i < NHUB; ++i) {
+            HubTask& H = sm.hub[i];
+            const unsigned v = *(volatile unsigned*)&H.ctl;
+            if ((v >> 24) != H_ACTIVE || (int)(v & H_SEG_MASK) >= *(volatile int*)&H.nseg) continue;
+            const unsigned old = atomicAdd(&H.ctl, 1u);
+            // a claim counts only if the task was live then; the task cannot
+            // be freed before this segment is done, so its fields stay valid
+            if ((old >> 24) == H_ACTIVE) {
+                __threadfence_block();
+                const int jj = (int)(old & H_SEG_MASK);
+                if (jj < H.nseg) {
+                    h = i;
+                    j = jj;
+                    break;
+                }
+            }
+        }
+    }
+    h = __shfl_sync(FULL, h, 0);
+    if (h < 0) return 0;
+    j = __shfl_sync(FULL, j, 0);
+    __threadfence_block();
+    HubTask& H = sm.hub[h];
+    const StepCtx c = H.c;
+    const long long end = c.beg + c.d;
+    const long long Q0a = (c.beg >> 2) & ~3ll, Q1 = (end + 3) >> 2;
+    const long long qa = Q0a + (long long)j * H.seg_q, qb = min(Q1, qa + H.seg_q);
+    WarpRes res;
+    res.init();
+    unsigned long long lane_sum = 0;
+    if (!scan_range<MODE>(g, c, qa, qb, end, lane, win, P, res, lane_sum, nullptr, (uint32_t)j, H.seed, H.qid, H.t))
+        return -1;
+    if (MODE == MODE_FAST) {
+        if (lane == 0 && res.sel >= 0)
+            atomicMin(&H.best, ((unsigned long long)__float_as_uint(res.tau) << 32) | (unsigned)res.sel);
+    } else {
+        const unsigned long long s = warp_sum_u64(lane_sum);
+        if (lane == 0) H.seg_sum[j] = s;
+    }
+    int last = 0;
+    if (lane == 0) {
+        __threadfence_block();
+        last = atomicAdd(&H.done_seg, 1) == H.nseg - 1;
+    }
+    last = __shfl_sync(FULL, last, 0);
+    if (last) {
+        __threadfence_block();
+        hub_finalize<MODE, NT>(g, reqs, sm, H, lane, win, cnt);
+    }
+    return 1;
+}
+
+// Per-warp dynamic shared memory: the TMA ring, the node2vec window, (exact
+// mode) the chunk sums, the ring's barriers and direct flags.
+template <int MODE>
+struct WarpSmem {
+    static constexpr int WIN_OFF = NST * STAGE_BYTES;
+    static constexpr int SUMS_OFF = WIN_OFF + WIN * 4;
+    static constexpr int BAR_OFF = SUMS_OFF + (MODE == MODE_EXACT ? NCHUNK_MAX * 8 : 0);
+    static constexpr int DIRECT_OFF = BAR_OFF + NST * 8;
+    static constexpr int BYTES = (DIRECT_OFF + NST * 4 + 127) & ~127;
+};
+
 // ------------------------------------------------------------- the engine
 
+// Resident CTAs per SM the register budget is cut for (24 warps per SM).
+constexpr int min_ctas(int nt) { return nt >= 512 ? 1 : (nt >= 256 ? 3 : 6); }
+
 template <int MODE, int NT>
-__global__ void __launch_bounds__(NT) walk_kernel(GraphDev g, const __grid_constant__ ReqTable tab,
-                                                  int n_req, long long total, Scratch* scratch,
-                                                  int slots, int d_warp) {
-    constexpr int NW = NT / 32;
+__global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, const __grid_constant__ ReqTable tab, int n_req,
+                                                  long long total, Scratch* scratch, int sw, int d_t, int seg_q) {
     const ReqDev* __restrict__ reqs = tab.ext ? tab.ext : tab.r;
     __shared__ Smem<NT> sm;
-    extern __shared__ __align__(16) uint32_t dyn[];  // exact mode: NW x d_warp weights
+    // dynamic shared memory per warp: the node2vec window (WIN ints) and, in
+    // exact mode, the warp sampler's chunk sums
+    extern __shared__ __align__(128) unsigned char dyn[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    unsigned char* mine = dyn + warp * WarpSmem<MODE>::BYTES;
+    int* win = reinterpret_cast<int*>(mine + WarpSmem<MODE>::WIN_OFF);
+    unsigned long long* chunk_sums = reinterpret_cast<unsigned long long*>(mine + WarpSmem<MODE>::SUMS_OFF);
+    WarpPipe P;
+    P.buf = mine;
+    P.bar = reinterpret_cast<unsigned long long*>(mine + WarpSmem<MODE>::BAR_OFF);
+    P.direct = reinterpret_cast<int*>(mine + WarpSmem<MODE>::DIRECT_OFF);
+    P.seq = 0;
+    if (lane < NST) mbar_init(&P.bar[lane], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 
-    for (int s = tid; s < S_MAX; s += NT) sm.state[s] = ST_EMPTY;
-    if (tid < C_NUM) sm.cnt[tid] = 0;
-    if (tid == 0) sm.exhausted = 0;
+    for (int i = tid; i < Smem<NT>::NS; i += NT) sm.state[i] = ST_EMPTY;
+    if (tid < NHUB) sm.hub[tid].ctl = (unsigned)H_FREE << 24;
+    if (tid == 0) sm.abort_flag = 0;
     __syncthreads();
 
+    Counters cnt;
+    cnt.clear();
+    const int s0 = warp * SW_MAX;
+    bool exhausted = false;
+    int rr = 0;
+    unsigned long long idle_since = 0;
+
     for (;;) {
-        // ---- 1. claim queries for empty slots (one atomic per CTA) ----
-        {
-            const bool empty = tid < slots && sm.state[tid] == ST_EMPTY;
-            const unsigned m = __ballot_sync(0xffffffffu, empty);
-            if (lane == 0 && warp < S_MAX / 32) sm.warp_empty[warp] = __popc(m);
-            __syncthreads();
-            if (tid == 0) {
-                int n_empty = 0;
-                for (int w = 0; w < (slots + 31) / 32; ++w) {
-                    const int e = sm.warp_empty[w];
-                    sm.warp_empty[w] = n_empty;  // exclusive prefix
-                    n_empty += e;
-                }
-                sm.claim_n = 0;
-                if (!sm.exhausted && n_empty > 0) {
-                    const unsigned long long base = atomicAdd(&scratch->cursor, (unsigned long long)n_empty);
-                    sm.claim_base = base;
-                    if (base >= (unsigned long long)total) {
-                        sm.exhausted = 1;
-                    } else {
-                        const unsigned long long left = (unsigned long long)total - base;
-                        sm.claim_n = (int)(left < (unsigned long long)n_empty ? left : n_empty);
-                        if (left <= (unsigned long long)n_empty) sm.exhausted = 1;
-                    }
-                }
-                sm.n_small = sm.n_large = sm.n_fin = sm.n_active = 0;
-            }
-            __syncthreads();
-            // ---- 2. initialise the claimed slots ----
-            if (empty) {
-                const int rank = sm.warp_empty[warp] + __popc(m & ((1u << lane) - 1u));
-                if (rank < sm.claim_n) {
-                    const long long gq = (long long)sm.claim_base + rank;
+        // ---- help the CTA's hub tasks first: their owners are waiting ----
+        const int hr = hub_help<MODE, NT>(g, reqs, sm, lane, win, P, cnt);
+        if (hr < 0) {
+            if (lane == 0) atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
+            break;
+        }
+        if (hr > 0) {
+            idle_since = 0;
+            continue;
+        }
+        // ---- pick a walk: refill empty slots, retire finished ones ----
+        int s = -1;
+        bool waiting = false;
+        for (int i = 0; i < sw; ++i) {
+            const int j = s0 + (rr + i) % sw;
+            // another warp may flip a hub-parked slot at any time: let lane 0
+            // read it once for the whole warp
+            int st = __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.state[j] : 0, 0);
+            if (st == ST_EMPTY && !exhausted) {
+                // claim one query (lane 0) and initialise the slot
+                long long gq = 0;
+                if (lane == 0) gq = (long long)atomicAdd(&scratch->cursor, 1ull);
+                gq = __shfl_sync(FULL, gq, 0);
+                if (gq >= total) {
+                    exhausted = true;
+                } else if (lane == 0) {
                     const int r = find_req(reqs, n_req, gq);
                     const ReqDev& R = reqs[r];
-                    const long long i = gq - R.q_begin;
-                    const int start = __ldg(R.starts + i);
-                    const int pv = R.prev ? __ldg(R.prev + i) : -1;
-                    const int t0 = R.step0 ? __ldg(R.step0 + i) : 0;
-                    int lim = R.lengths ? __ldg(R.lengths + i) : R.max_len;
+                    const long long qi = gq - R.q_begin;
+                    const int start = __ldg(R.starts + qi);
+                    const int pv = R.prev ? __ldg(R.prev + qi) : -1;
+                    const int t0 = R.step0 ? __ldg(R.step0 + qi) : 0;
+                    int lim = R.lengths ? __ldg(R.lengths + qi) : R.max_len;
                     lim = min(lim, R.max_len);
-                    sm.q[tid] = i;
-                    sm.req[tid] = r;
-                    sm.k[tid] = 0;
+                    sm.q[j] = qi;
+                    sm.req[j] = r;
+                    sm.k[j] = 0;
                     if (start < 0 || start >= g.n || pv < -1 || pv >= g.n || t0 < 0) {
                         atomicAdd(&scratch->counters[C_BAD_INPUT], 1ull);
-                        sm.state[tid] = ST_FINISH;  // written out as an empty path
+                        st = ST_FINISH;  // written out as an empty path
                     } else {
-                        R.paths[i * ((long long)R.max_len + 1)] = start;
-                        sm.k[tid] = 1;
-                        sm.cur[tid] = start;
-                        sm.prev[tid] = pv;
-                        sm.t[tid] = t0;
-                        sm.lim[tid] = lim;
+                        R.paths[qi * ((long long)R.max_len + 1)] = start;
+                        sm.k[j] = 1;
+                        sm.cur[j] = start;
+                        sm.prev[j] = pv;
+                        sm.t[j] = t0;
+                        sm.lim[j] = lim;
                         if (pv >= 0) {
                             const long long pb = __ldg(g.row_ptr + pv);
-                            sm.pbeg[tid] = pb;
-                            sm.pdeg[tid] = (int)(__ldg(g.row_ptr + pv + 1) - pb);
+                            sm.pbeg[j] = pb;
+                            sm.pdeg[j] = (int)(__ldg(g.row_ptr + pv + 1) - pb);
                         } else {
-                            sm.pbeg[tid] = 0;
-                            sm.pdeg[tid] = 0;
+                            sm.pbeg[j] = 0;
+                            sm.pdeg[j] = 0;
                         }
-                        sm.state[tid] = ST_ACTIVE;
+                        st = ST_READY;
+                    }
+                    sm.state[j] = st;
+                }
+                __syncwarp();
+                st = __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.state[j] : 0, 0);
+            }
+            if (st == ST_FINISH) {
+                // retire: path_len and -1 padding
+                const ReqDev& R = reqs[sm.req[j]];
+                const long long width = (long long)R.max_len + 1;
+                const int k = sm.k[j];
+                int32_t* row = R.paths + sm.q[j] * width;
+                for (long long e = k + lane; e < width; e += 32) row[e] = -1;
+                if (lane == 0) {
+                    R.path_len[sm.q[j]] = k;
+                    cnt.v[C_WALKS] += 1;
+                    sm.state[j] = ST_EMPTY;
+                }
+                __syncwarp();
+                --i;  // revisit this slot: it can be refilled now
+                continue;
+            }
+            if (st == ST_HUB) waiting = true;
+            if (st == ST_READY) {
+                s = j;
+                rr = (j - s0 + 1) % sw;
+                break;
+            }
+        }
+        if (s < 0) {
+            if (!waiting) break;  // all slots empty and no more queries
+            // only hub-parked walks left: help (above) or wait for them, bounded
+            if (idle_since == 0) {
+                idle_since = global_timer_ns();
+            } else if (__shfl_sync(FULL, (int)(global_timer_ns() - idle_since > kWaitLimitNs), 0)) {
+                if (lane == 0) {
+                    atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
+                    sm.abort_flag = 1;
+                }
+                break;
+            }
+            if (__shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.abort_flag : 0, 0)) break;
+            __nanosleep(200);
+            continue;
+        }
+        idle_since = 0;
+
+        // ---- one step of slot s ----
+        const ReqDev& R = reqs[sm.req[s]];
+        if (sm.t[s] >= sm.lim[s]) {
+            if (lane == 0) sm.state[s] = ST_FINISH;
+            __syncwarp();
+            continue;
+        }
+        const int v = sm.cur[s];
+        const long long beg = __ldg(g.row_ptr + v);
+        const int d = (int)(__ldg(g.row_ptr + v + 1) - beg);
+        if (d == 0) {  // dead end
+            if (lane == 0) sm.state[s] = ST_FINISH;
+            __syncwarp();
+            continue;
+        }
+        const StepCtx c = make_ctx(sm, R, s, beg, d);
+        const uint32_t t = (uint32_t)sm.t[s];
+        const uint64_t qid = (uint64_t)(R.q_id0 + sm.q[s]);
+        const long long end = beg + d;
+        const long long Q0 = (beg >> 2) & ~3ll, Q1 = (end + 3) >> 2;  // chunk grid aligned to 16 entries
+
+        // exact mode keeps one sum per 128-entry chunk: a row spanning more
+        // chunks than that goes to the CTA sampler whatever d_t says
+        const bool too_long = MODE == MODE_EXACT && Q1 - Q0 > (long long)CHQ * NCHUNK_MAX;
+        if (d > d_t || too_long) {
+            // publish as a CTA hub task, if a task entry is free
+            int h = -1;
+            if (lane == 0) {
+                for (int i = 0; i < NHUB; ++i) {
+                    const unsigned v = *(volatile unsigned*)&sm.hub[i].ctl;
+                    if ((v >> 24) == H_FREE && atomicCAS(&sm.hub[i].ctl, v, (unsigned)H_SETUP << 24) == v) {
+                        h = i;
+                        break;
                     }
                 }
-            }
-        }
-        // ---- 3. route every active walk by the degree of its vertex ----
-        if (tid < slots) {
-            int st = sm.state[tid];
-            if (st == ST_ACTIVE) {
-                if (sm.t[tid] >= sm.lim[tid]) {
-                    st = ST_FINISH;
-                } else {
-                    const int v = sm.cur[tid];
-                    const long long b = __ldg(g.row_ptr + v);
-                    const long long d = __ldg(g.row_ptr + v + 1) - b;
-                    sm.beg[tid] = b;
-                    sm.deg[tid] = (int)d;
-                    if (d == 0) st = ST_FINISH;  // dead end
-                    else if (d <= d_warp) sm.small_list[atomicAdd(&sm.n_small, 1)] = tid;
-                    else sm.large_list[atomicAdd(&sm.n_large, 1)] = tid;
+                if (h >= 0) {
+                    HubTask& H = sm.hub[h];
+                    const long long nq = Q1 - Q0;
+                    long long sq = max((long long)seg_q, (nq + NSEG_MAX - 1) / NSEG_MAX);
+                    sq = (sq + 31) & ~31ll;
+                    H.slot = s;
+                    H.seg_q = (int)sq;
+                    H.nseg = (int)((nq + sq - 1) / sq);
+                    H.done_seg = 0;
+                    H.best = ~0ull;
+                    H.c = c;
+                    H.seed = R.seed;
+                    H.qid = qid;
+                    H.t = t;
+                    H.req = sm.req[s];
+                    sm.state[s] = ST_HUB;
+                    __threadfence_block();
+                    atomicExch(&H.ctl, (unsigned)H_ACTIVE << 24);
                 }
-                sm.state[tid] = st;
             }
-            if (st == ST_FINISH) sm.fin_list[atomicAdd(&sm.n_fin, 1)] = tid;
+            h = __shfl_sync(FULL, h, 0);
+            if (h >= 0) continue;  // the walk waits for the CTA sampler; go on with other work
+            if (too_long) continue;  // no free entry: retry after helping the open ones
         }
-        __syncthreads();
-        if (sm.n_small + sm.n_large + sm.n_fin == 0 && sm.exhausted) break;
 
-        // ---- 4. retire finished walks: path_len and -1 padding ----
-        for (int f = warp; f < sm.n_fin; f += NW) {
-            const int s = sm.fin_list[f];
-            const ReqDev& R = reqs[sm.req[s]];
-            const long long width = (long long)R.max_len + 1;
-            const int k = sm.k[s];
-            int32_t* row = R.paths + sm.q[s] * width;
-            for (long long j = k + lane; j < width; j += 32) row[j] = -1;
-            if (lane == 0) {
-                R.path_len[sm.q[s]] = k;
-                sm.state[s] = ST_EMPTY;
-                atomicAdd(&sm.cnt[C_WALKS], 1ull);
+        // ---- warp sampler ----
+        WarpRes res;
+        res.init();
+        unsigned long long lane_sum = 0;
+        int sel = -1;
+        uint32_t oz = 0xFFFFFFFFu;
+        bool ok;
+        if (MODE == MODE_FAST) {
+            ok = scan_range<MODE>(g, c, Q0, Q1, end, lane, win, P, res, lane_sum, nullptr, 0u, R.seed, qid, t);
+            sel = res.sel;
+            if (sel >= 0 && R.algo == FW_PPR) oz = step_block(R.seed, qid, t).z;
+        } else {
+            // at most NCHUNK_MAX chunks here (longer rows went to the CTA sampler)
+            ok = scan_range<MODE>(g, c, Q0, Q1, end, lane, win, P, res, lane_sum, chunk_sums, 0u, R.seed, qid, t);
+            const unsigned long long W = ok ? warp_sum_u64(lane_sum) : 0ull;
+            __syncwarp();
+            if (W != 0) {
+                const uint4 o = step_block(R.seed, qid, t);
+                oz = o.z;
+                const unsigned long long x = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
+                unsigned long long r = __umul64hi(x, W);
+                const int nch = (int)((Q1 - Q0 + CHQ - 1) / CHQ);
+                const int ci = find_crossing(chunk_sums, nch, r, lane);
+                if (ci >= 0) {  // always, as r < W; the guard keeps every read inside the row
+                    const long long qa = Q0 + (long long)CHQ * ci;
+                    sel = exact_find(g, c, qa, min(Q1, qa + CHQ), end, r, lane, win);
+                }
             }
         }
-        // ---- 5. warp samplers: one step for every small task ----
-        for (int i = warp; i < sm.n_small; i += NW)
-            warp_step<MODE, NT>(g, reqs, sm, sm.small_list[i], dyn + warp * d_warp, lane);
-        __syncthreads();
-        // ---- 6. CTA sampler: one step for each large task in turn ----
-        const int nl = sm.n_large;
-        for (int i = 0; i < nl; ++i) block_step<MODE, NT>(g, reqs, sm, sm.large_list[i]);
-        __syncthreads();
+        if (!ok) {
+            if (lane == 0) atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
+            break;
+        }
+        if (lane == 0) {
+            if (sel < 0) {
+                sm.state[s] = ST_FINISH;  // nothing selectable: the walk stops here
+            } else {
+                cnt.step(d, c.algo, false);
+                commit(g, sm, R, s, c, __ldg(g.col + beg + sel), oz);
+            }
+        }
+        __syncwarp();
     }
-    if (tid < C_NUM && sm.cnt[tid]) atomicAdd(&scratch->counters[tid], sm.cnt[tid]);
+    if (lane == 0)
+        for (int i = 0; i < C_NUM; ++i)
+            if (cnt.v[i]) atomicAdd(&scratch->counters[i], cnt.v[i]);
 }
 
 template <int MODE, int NT>
 cudaError_t launch_one(const GraphDev& g, const ReqTable& reqs, int n_req, int64_t total, Scratch* scratch,
                        const Tuning& tu, cudaStream_t stream) {
     auto kern = walk_kernel<MODE, NT>;
-    const size_t dyn = MODE == MODE_EXACT ? (size_t)(NT / 32) * tu.d_warp * sizeof(uint32_t) : 0;
+    const size_t dyn = (size_t)(NT / 32) * WarpSmem<MODE>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, per_sm = 0;
@@ -569,27 +1114,28 @@ cudaError_t launch_one(const GraphDev& g, const ReqTable& reqs, int n_req, int64
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (tu.ctas_per_sm > 0) per_sm = min(per_sm, tu.ctas_per_sm);
+    const int sw = max(1, min(SW_MAX, tu.slots / (NT / 32)));
     long long grid = (long long)sms * per_sm;
-    const long long need = (total + tu.slots - 1) / tu.slots;
+    const long long need = (total + (long long)sw * (NT / 32) - 1) / ((long long)sw * (NT / 32));
     if (need < grid) grid = need > 0 ? need : 1;
-    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, reqs, n_req, (long long)total, scratch, tu.slots,
-                                                tu.d_warp);
+    int d_t = tu.d_warp;
+    if (MODE == MODE_EXACT) d_t = min(d_t, NCHUNK_MAX * 128 - 8);  // at most NCHUNK_MAX chunks
+    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, reqs, n_req, (long long)total, scratch, sw, d_t, 1024);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-Tuning default_tuning() { return Tuning{256, 64, 1024, 0}; }
+Tuning default_tuning() { return Tuning{256, 16, 8192, 0}; }
 
 Tuning sanitize_tuning(Tuning t) {
     const Tuning d = default_tuning();
     if (t.block_threads != 128 && t.block_threads != 256 && t.block_threads != 512) t.block_threads = d.block_threads;
     if (t.slots <= 0) t.slots = d.slots;
-    if (t.slots > S_MAX) t.slots = S_MAX;
-    if (t.slots > t.block_threads) t.slots = t.block_threads;
+    if (t.slots > (t.block_threads / 32) * SW_MAX) t.slots = (t.block_threads / 32) * SW_MAX;
     if (t.d_warp <= 0) t.d_warp = d.d_warp;
-    if (t.d_warp > 4096) t.d_warp = 4096;
-    t.d_warp = (t.d_warp + 31) & ~31;
+    if (t.d_warp < 128) t.d_warp = 128;
+    if (t.d_warp > (1 << 30)) t.d_warp = 1 << 30;
     if (t.ctas_per_sm < 0) t.ctas_per_sm = 0;
     return t;
 }

@@ -127,7 +127,9 @@ def test_T4_hub_block_tier(orc):
     cur = int((g.row_ptr[1:] - g.row_ptr[:-1]).argmax())
     nxt = _one_step(dg, "weighted", cur, -1, 0, 20240416)
     st = dg.stats()
-    assert st["block_steps"] == N
+    # hub rows go to the CTA sampler unless all of the CTA's hub-task entries
+    # are taken, in which case the owner warp samples the row itself
+    assert st["block_steps"] > N // 2 and st["block_steps"] + st["warp_steps"] == N
     tv, pv = _compare(g, nxt, _law(orc, g, "weighted", cur, -1, 0), cur, bins=64)
     assert tv <= TV_MAX and pv > P_MIN, (tv, pv)
 
