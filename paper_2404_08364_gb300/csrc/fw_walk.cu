@@ -167,10 +167,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t 
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)  // let the thread sleep up to 20 us for the phase
         : "memory");
     return ok != 0;
 }
@@ -402,12 +402,13 @@ __device__ __forceinline__ void n2v_apply(const GraphDev& g, const StepCtx& cx, 
 // before the next record is Exp(1) / tau; the record's own time is the race
 // time conditioned to lie below tau.  Every lane holds the same state: a
 // chunk costs one warp prefix sum and one comparison unless a record falls
-// inside it, and a row of d entries makes about ln d records.  X is kept in
-// double so that subtracting many chunk totals does not drift.
+// inside it, and a row of d entries makes about ln d records.  X is kept as
+// an unevaluated sum of two FP32 numbers so that subtracting many chunk
+// totals does not drift (FP64 is a slow pipe on this part).
 struct WarpRes {
     float tau;
     int sel;
-    double X;
+    float Xh, Xl;  // X as an unevaluated FP32 sum Xh + Xl
     uint32_t ctr;
     uint32_t spare0, spare1;
     uint32_t has_spare;
@@ -415,7 +416,8 @@ struct WarpRes {
     __device__ __forceinline__ void init() {
         tau = __int_as_float(0x7f800000);  // +inf
         sel = -1;
-        X = 0.0;
+        Xh = 0.0f;
+        Xl = 0.0f;
         ctr = 0;
         has_spare = 0;
     }
@@ -443,7 +445,8 @@ __device__ __noinline__ WarpRes warp_record(WarpRes r, int idx, float w, uint64_
     else e = -log1pf(u1 * expm1f(-w * r.tau));
     r.tau = e / w;
     r.sel = idx;
-    r.X = (double)(-logf(u2)) / (double)r.tau;
+    r.Xh = -logf(u2) / r.tau;
+    r.Xl = 0.0f;
     return r;
 }
 
@@ -459,22 +462,26 @@ __device__ __forceinline__ void warp_offer_chunk(WarpRes& R, const float (&w)[4]
         if (lane >= o) incl += n;
     }
     const float tot = __shfl_sync(FULL, incl, 31);
-    if (R.X > (double)tot) {  // no record in this chunk (the common case)
-        R.X -= (double)tot;
+    if (R.Xh - tot + R.Xl > 0.0f) {  // no record in this chunk (the common case)
+        // X -= tot with the rounding error kept (Fast2Sum: |Xh| > tot here)
+        const float sh = R.Xh - tot;
+        R.Xl += (R.Xh - sh) - tot;
+        R.Xh = sh;
         return;
     }
     const float excl = incl - l3;
     const float cum[4] = {excl + l0, excl + l1, excl + l2, excl + l3};
-    double target = R.X;  // a record falls on the first entry whose cumulative weight reaches target
-    int last = -1;        // chunk position (lane * 4 + j) of the last record: each record lies beyond it
+    float target = R.Xh + R.Xl;  // a record falls on the first entry whose cumulative weight reaches target
+    int last = -1;               // chunk position (lane * 4 + j) of the last record: each record lies beyond it
     for (;;) {
         int jj = -1;
 #pragma unroll
         for (int j = 3; j >= 0; --j)
-            if (lane * 4 + j > last && w[j] > 0.0f && (double)cum[j] >= target) jj = j;
+            if (lane * 4 + j > last && w[j] > 0.0f && cum[j] >= target) jj = j;
         const unsigned m = __ballot_sync(FULL, jj >= 0);
         if (!m) {
-            R.X = target - (double)tot;
+            R.Xh = target - tot;
+            R.Xl = 0.0f;
             return;
         }
         const int L = __ffs(m) - 1;
@@ -490,7 +497,7 @@ __device__ __forceinline__ void warp_offer_chunk(WarpRes& R, const float (&w)[4]
         const int idx = __shfl_sync(FULL, e0 + jj, L);
         last = L * 4 + __shfl_sync(FULL, jj, L);
         R = warp_record(R, idx, wr, seed, qid, t, stream);
-        target = (double)cr + R.X;
+        target = cr + R.Xh;
     }
 }
 
@@ -553,10 +560,10 @@ __device__ __forceinline__ void stage_quad(const GraphDev& g, const StepCtx& c, 
     }
     const int et = c.algo == FW_METAPATH ? *reinterpret_cast<const int*>(b + ST_ET + lane * 4) : 0;
     Q.valid = 0;
+    const int rel = (int)((q << 2) - c.beg);  // row index of entry 0 of the quad
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const long long e = (q << 2) + j;
-        if (e >= c.beg && e < end) {
+        if ((unsigned)(rel + j) < (unsigned)c.d) {
             Q.valid |= 1u << j;
             if (c.algo == FW_METAPATH && (int)(int8_t)(et >> (8 * j)) != c.want) Q.w[j] = 0;
         } else {
@@ -853,11 +860,8 @@ struct WarpSmem {
 
 // ------------------------------------------------------------- the engine
 
-// Resident CTAs per SM the register budget is cut for (24 warps per SM).
-constexpr int min_ctas(int nt) { return nt >= 512 ? 1 : (nt >= 256 ? 3 : 6); }
-
 template <int MODE, int NT>
-__global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, const __grid_constant__ ReqTable tab, int n_req,
+__global__ void __launch_bounds__(NT) walk_kernel(GraphDev g, const __grid_constant__ ReqTable tab, int n_req,
                                                   long long total, Scratch* scratch, int sw, int d_t, int seg_q) {
     const ReqDev* __restrict__ reqs = tab.ext ? tab.ext : tab.r;
     __shared__ Smem<NT> sm;
