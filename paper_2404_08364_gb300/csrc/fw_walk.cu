@@ -198,14 +198,22 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
 // A warp's private ring of NST chunk buffers in shared memory, each with its
 // mbarrier and a flag telling whether the chunk came by TMA (0) or must be
 // read from global memory (1: it touches the unpadded end of the arrays).
-// `seq` counts the chunks the warp has ever issued: chunk seq lives in stage
-// seq % NST and completes phase (seq / NST) & 1 of that stage's barrier.
+// Chunks go through the stages in order; (st, ph) = stage of the next chunk
+// to consume and the barrier phase parity it completes there.
 struct WarpPipe {
     unsigned char* buf;
     unsigned long long* bar;
     int* direct;
-    uint32_t seq;
+    int st;
+    uint32_t ph;
 };
+
+__device__ __forceinline__ void ring_next(int& st, uint32_t& ph) {
+    if (++st == NST) {
+        st = 0;
+        ph ^= 1u;
+    }
+}
 
 // --------------------------------------------------------------------------
 // node2vec membership: is a neighbour u of cur also in N(prev)?  Both rows are
@@ -512,12 +520,11 @@ __device__ __forceinline__ int pick_in_quad(const uint32_t (&w)[4], unsigned lon
     return 3;
 }
 
-// Lane 0: start loading chunk number `seq` (quads [qs, qs + nq), qs a
-// multiple of 4) into its stage of the warp's ring.
+// Lane 0: start loading quads [qs, qs + nq) (qs a multiple of 4) into stage
+// st of the warp's ring.
 template <int MODE>
-__device__ __forceinline__ void pipe_issue(const GraphDev& g, WarpPipe& P, uint32_t seq, long long qs, int nq,
+__device__ __forceinline__ void pipe_issue(const GraphDev& g, WarpPipe& P, int st, long long qs, int nq,
                                            bool labels) {
-    const int st = seq % NST;
     unsigned char* b = P.buf + st * STAGE_BYTES;
     const long long nq4 = (nq + 3) & ~3;
     if (4 * (qs + nq4) <= g.m) {
@@ -586,23 +593,31 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
                                            uint64_t seed, uint64_t qid, uint32_t t) {
     const int nch = (int)((qb - qa + CHQ - 1) / CHQ);
     const bool labels = c.algo == FW_METAPATH;
-    if (lane == 0)
-        for (int k = 0; k < nch && k < NST; ++k)
-            pipe_issue<MODE>(g, P, P.seq + k, qa + (long long)k * CHQ, (int)min((long long)CHQ, qb - qa - (long long)k * CHQ), labels);
+    if (lane == 0) {
+        int ist = P.st;
+        uint32_t iph = P.ph;
+        for (int k = 0; k < nch && k < NST; ++k) {
+            pipe_issue<MODE>(g, P, ist, qa + (long long)k * CHQ, (int)min((long long)CHQ, qb - qa - (long long)k * CHQ),
+                             labels);
+            ring_next(ist, iph);
+        }
+    }
     int pos = 0;
     bool ok = true;
     for (int k = 0; k < nch; ++k) {
-        const uint32_t sq = P.seq + k;
-        const int st = sq % NST;
+        const int st = P.st;
         const long long qs = qa + (long long)k * CHQ;
-        if (!mbar_wait_bounded(&P.bar[st], (sq / NST) & 1u)) ok = false;
+        if (!mbar_wait_bounded(&P.bar[st], P.ph)) ok = false;
         if (!__all_sync(FULL, ok)) {
-            ok = false;
             // let the copies already issued land before giving up
-            if (lane == 0)
-                for (int kk = k + 1; kk < nch && kk < k + NST; ++kk)
-                    mbar_wait_bounded(&P.bar[(P.seq + kk) % NST], ((P.seq + kk) / NST) & 1u);
-            P.seq += min(nch, k + NST);
+            if (lane == 0) {
+                int dst = st;
+                uint32_t dph = P.ph;
+                for (int kk = k + 1; kk < nch && kk < k + NST; ++kk) {
+                    ring_next(dst, dph);
+                    mbar_wait_bounded(&P.bar[dst], dph);
+                }
+            }
             return false;
         }
         Quad<MODE> cur;
@@ -610,8 +625,9 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
         __syncwarp();  // every lane has its quad: the stage may be refilled
         if (lane == 0 && k + NST < nch) {
             const long long qn = qa + (long long)(k + NST) * CHQ;
-            pipe_issue<MODE>(g, P, sq + NST, qn, (int)min((long long)CHQ, qb - qn), labels);
+            pipe_issue<MODE>(g, P, st, qn, (int)min((long long)CHQ, qb - qn), labels);
         }
+        ring_next(P.st, P.ph);
         n2v_apply<MODE>(g, c, cur, pos, lane, win);
         if (MODE == MODE_FAST) {
             const float wf[4] = {(float)cur.w[0], (float)cur.w[1], (float)cur.w[2], (float)cur.w[3]};
@@ -625,7 +641,6 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
             }
         }
     }
-    P.seq += nch;
     return ok;
 }
 
@@ -787,13 +802,12 @@ __device__ void hub_finalize(const GraphDev& g, const ReqDev* __restrict__ reqs,
     __syncwarp();
 }
 
-// Take one segment of an open hub task, if any, and sample it.  Returns 1 if
-// the warp did hub work, 0 if none was open, -1 if a copy never landed.
-// Warp-collective.
-template <int MODE, int NT>
-__device__ int hub_help(const GraphDev& g, const ReqDev* __restrict__ reqs, Smem<NT>& sm, int lane, int* win,
-                        WarpPipe& P, Counters& cnt) {
-    int h = -1, j = -1;
+// Claim one segment of an open hub task: (h, j) = task, segment; false if
+// none is open.  Warp-collective, uniform result.
+template <int NT>
+__device__ __forceinline__ bool hub_claim(Smem<NT>& sm, int lane, int& h, int& j) {
+    h = -1;
+    j = -1;
     if (lane == 0) {
         for (int i = 0; i < NHUB; ++i) {
             HubTask& H = sm.hub[i];
@@ -814,19 +828,17 @@ __device__ int hub_help(const GraphDev& g, const ReqDev* __restrict__ reqs, Smem
         }
     }
     h = __shfl_sync(FULL, h, 0);
-    if (h < 0) return 0;
     j = __shfl_sync(FULL, j, 0);
-    __threadfence_block();
-    HubTask& H = sm.hub[h];
-    const StepCtx c = H.c;
-    const long long end = c.beg + c.d;
-    const long long Q0a = (c.beg >> 2) & ~3ll, Q1 = (end + 3) >> 2;
-    const long long qa = Q0a + (long long)j * H.seg_q, qb = min(Q1, qa + H.seg_q);
-    WarpRes res;
-    res.init();
-    unsigned long long lane_sum = 0;
-    if (!scan_range<MODE>(g, c, qa, qb, end, lane, win, P, res, lane_sum, nullptr, (uint32_t)j, H.seed, H.qid, H.t))
-        return -1;
+    if (h >= 0) __threadfence_block();
+    return h >= 0;
+}
+
+// Fold a sampled segment into its hub task; the warp that completes the last
+// segment finishes the step.  Warp-collective.
+template <int MODE, int NT>
+__device__ __forceinline__ void hub_merge(const GraphDev& g, const ReqDev* __restrict__ reqs, Smem<NT>& sm,
+                                          HubTask& H, int j, const WarpRes& res, unsigned long long lane_sum,
+                                          int lane, int* win, Counters& cnt) {
     if (MODE == MODE_FAST) {
         if (lane == 0 && res.sel >= 0)
             atomicMin(&H.best, ((unsigned long long)__float_as_uint(res.tau) << 32) | (unsigned)res.sel);
@@ -844,7 +856,6 @@ __device__ int hub_help(const GraphDev& g, const ReqDev* __restrict__ reqs, Smem
         __threadfence_block();
         hub_finalize<MODE, NT>(g, reqs, sm, H, lane, win, cnt);
     }
-    return 1;
 }
 
 // Per-warp dynamic shared memory: the TMA ring, the node2vec window, (exact
@@ -876,7 +887,8 @@ __global__ void __launch_bounds__(NT) walk_kernel(GraphDev g, const __grid_const
     P.buf = mine;
     P.bar = reinterpret_cast<unsigned long long*>(mine + WarpSmem<MODE>::BAR_OFF);
     P.direct = reinterpret_cast<int*>(mine + WarpSmem<MODE>::DIRECT_OFF);
-    P.seq = 0;
+    P.st = 0;
+    P.ph = 0;
     if (lane < NST) mbar_init(&P.bar[lane], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 
@@ -893,208 +905,229 @@ __global__ void __launch_bounds__(NT) walk_kernel(GraphDev g, const __grid_const
     unsigned long long idle_since = 0;
 
     for (;;) {
-        // ---- help the CTA's hub tasks first: their owners are waiting ----
-        const int hr = hub_help<MODE, NT>(g, reqs, sm, lane, win, P, cnt);
-        if (hr < 0) {
-            if (lane == 0) atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
-            break;
-        }
-        if (hr > 0) {
-            idle_since = 0;
-            continue;
-        }
-        // ---- pick a walk: refill empty slots, retire finished ones ----
+        // ------------------------------------------------ choose the work
+        // Either one segment of an open hub task (their owners are waiting,
+        // so they come first) or one step of one of this warp's own walks.
+        StepCtx c;
+        long long qa, qb;
+        uint64_t seed, qid;
+        uint32_t t, stream;
+        unsigned long long* sums = nullptr;
+        int h, j;
         int s = -1;
-        bool waiting = false;
-        for (int i = 0; i < sw; ++i) {
-            const int j = s0 + (rr + i) % sw;
-            // another warp may flip a hub-parked slot at any time: let lane 0
-            // read it once for the whole warp
-            int st = __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.state[j] : 0, 0);
-            if (st == ST_EMPTY && !exhausted) {
-                // claim one query (lane 0) and initialise the slot
-                long long gq = 0;
-                if (lane == 0) gq = (long long)atomicAdd(&scratch->cursor, 1ull);
-                gq = __shfl_sync(FULL, gq, 0);
-                if (gq >= total) {
-                    exhausted = true;
-                } else if (lane == 0) {
-                    const int r = find_req(reqs, n_req, gq);
-                    const ReqDev& R = reqs[r];
-                    const long long qi = gq - R.q_begin;
-                    const int start = __ldg(R.starts + qi);
-                    const int pv = R.prev ? __ldg(R.prev + qi) : -1;
-                    const int t0 = R.step0 ? __ldg(R.step0 + qi) : 0;
-                    int lim = R.lengths ? __ldg(R.lengths + qi) : R.max_len;
-                    lim = min(lim, R.max_len);
-                    sm.q[j] = qi;
-                    sm.req[j] = r;
-                    sm.k[j] = 0;
-                    if (start < 0 || start >= g.n || pv < -1 || pv >= g.n || t0 < 0) {
-                        atomicAdd(&scratch->counters[C_BAD_INPUT], 1ull);
-                        st = ST_FINISH;  // written out as an empty path
-                    } else {
-                        R.paths[qi * ((long long)R.max_len + 1)] = start;
-                        sm.k[j] = 1;
-                        sm.cur[j] = start;
-                        sm.prev[j] = pv;
-                        sm.t[j] = t0;
-                        sm.lim[j] = lim;
-                        if (pv >= 0) {
-                            const long long pb = __ldg(g.row_ptr + pv);
-                            sm.pbeg[j] = pb;
-                            sm.pdeg[j] = (int)(__ldg(g.row_ptr + pv + 1) - pb);
+        const ReqDev* R = nullptr;
+        const bool seg = hub_claim<NT>(sm, lane, h, j);
+        if (seg) {
+            HubTask& H = sm.hub[h];
+            c = H.c;
+            const long long Q0a = (c.beg >> 2) & ~3ll, Q1 = (c.beg + c.d + 3) >> 2;
+            qa = Q0a + (long long)j * H.seg_q;
+            qb = min(Q1, qa + H.seg_q);
+            seed = H.seed;
+            qid = H.qid;
+            t = H.t;
+            stream = (uint32_t)j;
+        } else {
+            // ---- pick a walk: refill empty slots, retire finished ones ----
+            bool waiting = false;
+            for (int i = 0; i < sw; ++i) {
+                const int jj = s0 + (rr + i) % sw;
+                // another warp may flip a hub-parked slot at any time: let
+                // lane 0 read it once for the whole warp
+                int st = __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.state[jj] : 0, 0);
+                if (st == ST_EMPTY && !exhausted) {
+                    // claim one query (lane 0) and initialise the slot
+                    long long gq = 0;
+                    if (lane == 0) gq = (long long)atomicAdd(&scratch->cursor, 1ull);
+                    gq = __shfl_sync(FULL, gq, 0);
+                    if (gq >= total) {
+                        exhausted = true;
+                    } else if (lane == 0) {
+                        const int r = find_req(reqs, n_req, gq);
+                        const ReqDev& Rq = reqs[r];
+                        const long long qi = gq - Rq.q_begin;
+                        const int start = __ldg(Rq.starts + qi);
+                        const int pv = Rq.prev ? __ldg(Rq.prev + qi) : -1;
+                        const int t0 = Rq.step0 ? __ldg(Rq.step0 + qi) : 0;
+                        int lim = Rq.lengths ? __ldg(Rq.lengths + qi) : Rq.max_len;
+                        lim = min(lim, Rq.max_len);
+                        sm.q[jj] = qi;
+                        sm.req[jj] = r;
+                        sm.k[jj] = 0;
+                        if (start < 0 || start >= g.n || pv < -1 || pv >= g.n || t0 < 0) {
+                            atomicAdd(&scratch->counters[C_BAD_INPUT], 1ull);
+                            st = ST_FINISH;  // written out as an empty path
                         } else {
-                            sm.pbeg[j] = 0;
-                            sm.pdeg[j] = 0;
+                            Rq.paths[qi * ((long long)Rq.max_len + 1)] = start;
+                            sm.k[jj] = 1;
+                            sm.cur[jj] = start;
+                            sm.prev[jj] = pv;
+                            sm.t[jj] = t0;
+                            sm.lim[jj] = lim;
+                            if (pv >= 0) {
+                                const long long pb = __ldg(g.row_ptr + pv);
+                                sm.pbeg[jj] = pb;
+                                sm.pdeg[jj] = (int)(__ldg(g.row_ptr + pv + 1) - pb);
+                            } else {
+                                sm.pbeg[jj] = 0;
+                                sm.pdeg[jj] = 0;
+                            }
+                            st = ST_READY;
                         }
-                        st = ST_READY;
+                        sm.state[jj] = st;
                     }
-                    sm.state[j] = st;
+                    __syncwarp();
+                    st = __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.state[jj] : 0, 0);
                 }
-                __syncwarp();
-                st = __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.state[j] : 0, 0);
+                if (st == ST_FINISH) {
+                    // retire: path_len and -1 padding
+                    const ReqDev& Rq = reqs[sm.req[jj]];
+                    const long long width = (long long)Rq.max_len + 1;
+                    const int k = sm.k[jj];
+                    int32_t* row = Rq.paths + sm.q[jj] * width;
+                    for (long long e = k + lane; e < width; e += 32) row[e] = -1;
+                    if (lane == 0) {
+                        Rq.path_len[sm.q[jj]] = k;
+                        cnt.v[C_WALKS] += 1;
+                        sm.state[jj] = ST_EMPTY;
+                    }
+                    __syncwarp();
+                    --i;  // revisit this slot: it can be refilled now
+                    continue;
+                }
+                if (st == ST_HUB) waiting = true;
+                if (st == ST_READY) {
+                    s = jj;
+                    rr = (jj - s0 + 1) % sw;
+                    break;
+                }
             }
-            if (st == ST_FINISH) {
-                // retire: path_len and -1 padding
-                const ReqDev& R = reqs[sm.req[j]];
-                const long long width = (long long)R.max_len + 1;
-                const int k = sm.k[j];
-                int32_t* row = R.paths + sm.q[j] * width;
-                for (long long e = k + lane; e < width; e += 32) row[e] = -1;
-                if (lane == 0) {
-                    R.path_len[sm.q[j]] = k;
-                    cnt.v[C_WALKS] += 1;
-                    sm.state[j] = ST_EMPTY;
+            if (s < 0) {
+                if (!waiting) break;  // all slots empty and no more queries
+                // only hub-parked walks left: help (above) or wait for them, bounded
+                if (idle_since == 0) {
+                    idle_since = global_timer_ns();
+                } else if (__shfl_sync(FULL, (int)(global_timer_ns() - idle_since > kWaitLimitNs), 0)) {
+                    if (lane == 0) {
+                        atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
+                        sm.abort_flag = 1;
+                    }
+                    break;
                 }
-                __syncwarp();
-                --i;  // revisit this slot: it can be refilled now
+                if (__shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.abort_flag : 0, 0)) break;
+                __nanosleep(200);
                 continue;
             }
-            if (st == ST_HUB) waiting = true;
-            if (st == ST_READY) {
-                s = j;
-                rr = (j - s0 + 1) % sw;
-                break;
+
+            // ---- one step of slot s ----
+            R = &reqs[sm.req[s]];
+            if (sm.t[s] >= sm.lim[s]) {
+                if (lane == 0) sm.state[s] = ST_FINISH;
+                __syncwarp();
+                continue;
             }
-        }
-        if (s < 0) {
-            if (!waiting) break;  // all slots empty and no more queries
-            // only hub-parked walks left: help (above) or wait for them, bounded
-            if (idle_since == 0) {
-                idle_since = global_timer_ns();
-            } else if (__shfl_sync(FULL, (int)(global_timer_ns() - idle_since > kWaitLimitNs), 0)) {
+            const int v = sm.cur[s];
+            const long long beg = __ldg(g.row_ptr + v);
+            const int d = (int)(__ldg(g.row_ptr + v + 1) - beg);
+            if (d == 0) {  // dead end
+                if (lane == 0) sm.state[s] = ST_FINISH;
+                __syncwarp();
+                continue;
+            }
+            c = make_ctx(sm, *R, s, beg, d);
+            t = (uint32_t)sm.t[s];
+            qid = (uint64_t)(R->q_id0 + sm.q[s]);
+            seed = R->seed;
+            const long long end = beg + d;
+            qa = (beg >> 2) & ~3ll;  // chunk grid aligned to 16 entries
+            qb = (end + 3) >> 2;
+
+            // exact mode keeps one sum per 128-entry chunk: a row spanning
+            // more chunks than that goes to the CTA sampler whatever d_t says
+            const bool too_long = MODE == MODE_EXACT && qb - qa > (long long)CHQ * NCHUNK_MAX;
+            if (d > d_t || too_long) {
+                // publish as a CTA hub task, if a task entry is free
+                int hh = -1;
                 if (lane == 0) {
-                    atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
-                    sm.abort_flag = 1;
+                    for (int i = 0; i < NHUB; ++i) {
+                        const unsigned vv = *(volatile unsigned*)&sm.hub[i].ctl;
+                        if ((vv >> 24) == H_FREE &&
+                            atomicCAS(&sm.hub[i].ctl, vv, (unsigned)H_SETUP << 24) == vv) {
+                            hh = i;
+                            break;
+                        }
+                    }
+                    if (hh >= 0) {
+                        HubTask& H = sm.hub[hh];
+                        const long long nq = qb - qa;
+                        long long sq = max((long long)seg_q, (nq + NSEG_MAX - 1) / NSEG_MAX);
+                        sq = (sq + 31) & ~31ll;
+                        H.slot = s;
+                        H.seg_q = (int)sq;
+                        H.nseg = (int)((nq + sq - 1) / sq);
+                        H.done_seg = 0;
+                        H.best = ~0ull;
+                        H.c = c;
+                        H.seed = seed;
+                        H.qid = qid;
+                        H.t = t;
+                        H.req = sm.req[s];
+                        sm.state[s] = ST_HUB;
+                        __threadfence_block();
+                        atomicExch(&H.ctl, (unsigned)H_ACTIVE << 24);
+                    }
                 }
-                break;
+                hh = __shfl_sync(FULL, hh, 0);
+                if (hh >= 0) continue;   // the walk waits for the CTA sampler; go on with other work
+                if (too_long) continue;  // no free entry: retry after helping the open ones
             }
-            if (__shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.abort_flag : 0, 0)) break;
-            __nanosleep(200);
-            continue;
+            stream = 0;
+            if (MODE == MODE_EXACT) sums = chunk_sums;
         }
         idle_since = 0;
 
-        // ---- one step of slot s ----
-        const ReqDev& R = reqs[sm.req[s]];
-        if (sm.t[s] >= sm.lim[s]) {
-            if (lane == 0) sm.state[s] = ST_FINISH;
-            __syncwarp();
-            continue;
-        }
-        const int v = sm.cur[s];
-        const long long beg = __ldg(g.row_ptr + v);
-        const int d = (int)(__ldg(g.row_ptr + v + 1) - beg);
-        if (d == 0) {  // dead end
-            if (lane == 0) sm.state[s] = ST_FINISH;
-            __syncwarp();
-            continue;
-        }
-        const StepCtx c = make_ctx(sm, R, s, beg, d);
-        const uint32_t t = (uint32_t)sm.t[s];
-        const uint64_t qid = (uint64_t)(R.q_id0 + sm.q[s]);
-        const long long end = beg + d;
-        const long long Q0 = (beg >> 2) & ~3ll, Q1 = (end + 3) >> 2;  // chunk grid aligned to 16 entries
-
-        // exact mode keeps one sum per 128-entry chunk: a row spanning more
-        // chunks than that goes to the CTA sampler whatever d_t says
-        const bool too_long = MODE == MODE_EXACT && Q1 - Q0 > (long long)CHQ * NCHUNK_MAX;
-        if (d > d_t || too_long) {
-            // publish as a CTA hub task, if a task entry is free
-            int h = -1;
-            if (lane == 0) {
-                for (int i = 0; i < NHUB; ++i) {
-                    const unsigned v = *(volatile unsigned*)&sm.hub[i].ctl;
-                    if ((v >> 24) == H_FREE && atomicCAS(&sm.hub[i].ctl, v, (unsigned)H_SETUP << 24) == v) {
-                        h = i;
-                        break;
-                    }
-                }
-                if (h >= 0) {
-                    HubTask& H = sm.hub[h];
-                    const long long nq = Q1 - Q0;
-                    long long sq = max((long long)seg_q, (nq + NSEG_MAX - 1) / NSEG_MAX);
-                    sq = (sq + 31) & ~31ll;
-                    H.slot = s;
-                    H.seg_q = (int)sq;
-                    H.nseg = (int)((nq + sq - 1) / sq);
-                    H.done_seg = 0;
-                    H.best = ~0ull;
-                    H.c = c;
-                    H.seed = R.seed;
-                    H.qid = qid;
-                    H.t = t;
-                    H.req = sm.req[s];
-                    sm.state[s] = ST_HUB;
-                    __threadfence_block();
-                    atomicExch(&H.ctl, (unsigned)H_ACTIVE << 24);
-                }
-            }
-            h = __shfl_sync(FULL, h, 0);
-            if (h >= 0) continue;  // the walk waits for the CTA sampler; go on with other work
-            if (too_long) continue;  // no free entry: retry after helping the open ones
-        }
-
-        // ---- warp sampler ----
+        // ------------------------------------ stream the row range (one site)
         WarpRes res;
         res.init();
         unsigned long long lane_sum = 0;
+        const long long end = c.beg + c.d;
+        if (!scan_range<MODE>(g, c, qa, qb, end, lane, win, P, res, lane_sum, sums, stream, seed, qid, t)) {
+            if (lane == 0) atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
+            break;
+        }
+
+        // ------------------------------------------------ use the result
+        if (seg) {
+            hub_merge<MODE, NT>(g, reqs, sm, sm.hub[h], j, res, lane_sum, lane, win, cnt);
+            continue;
+        }
         int sel = -1;
         uint32_t oz = 0xFFFFFFFFu;
-        bool ok;
         if (MODE == MODE_FAST) {
-            ok = scan_range<MODE>(g, c, Q0, Q1, end, lane, win, P, res, lane_sum, nullptr, 0u, R.seed, qid, t);
             sel = res.sel;
-            if (sel >= 0 && R.algo == FW_PPR) oz = step_block(R.seed, qid, t).z;
+            if (sel >= 0 && R->algo == FW_PPR) oz = step_block(seed, qid, t).z;
         } else {
-            // at most NCHUNK_MAX chunks here (longer rows went to the CTA sampler)
-            ok = scan_range<MODE>(g, c, Q0, Q1, end, lane, win, P, res, lane_sum, chunk_sums, 0u, R.seed, qid, t);
-            const unsigned long long W = ok ? warp_sum_u64(lane_sum) : 0ull;
+            const unsigned long long W = warp_sum_u64(lane_sum);
             __syncwarp();
             if (W != 0) {
-                const uint4 o = step_block(R.seed, qid, t);
+                const uint4 o = step_block(seed, qid, t);
                 oz = o.z;
                 const unsigned long long x = (unsigned long long)o.x | ((unsigned long long)o.y << 32);
                 unsigned long long r = __umul64hi(x, W);
-                const int nch = (int)((Q1 - Q0 + CHQ - 1) / CHQ);
+                const int nch = (int)((qb - qa + CHQ - 1) / CHQ);
                 const int ci = find_crossing(chunk_sums, nch, r, lane);
                 if (ci >= 0) {  // always, as r < W; the guard keeps every read inside the row
-                    const long long qa = Q0 + (long long)CHQ * ci;
-                    sel = exact_find(g, c, qa, min(Q1, qa + CHQ), end, r, lane, win);
+                    const long long q0 = qa + (long long)CHQ * ci;
+                    sel = exact_find(g, c, q0, min(qb, q0 + CHQ), end, r, lane, win);
                 }
             }
-        }
-        if (!ok) {
-            if (lane == 0) atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
-            break;
         }
         if (lane == 0) {
             if (sel < 0) {
                 sm.state[s] = ST_FINISH;  // nothing selectable: the walk stops here
             } else {
-                cnt.step(d, c.algo, false);
-                commit(g, sm, R, s, c, __ldg(g.col + beg + sel), oz);
+                cnt.step(c.d, c.algo, false);
+                commit(g, sm, *R, s, c, __ldg(g.col + c.beg + sel), oz);
             }
         }
         __syncwarp();
