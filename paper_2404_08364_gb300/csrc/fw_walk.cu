@@ -250,8 +250,27 @@ __device__ __forceinline__ int lower_bound_from(const int32_t* __restrict__ B, i
     return lo + __popc(__ballot_sync(FULL, v < x));
 }
 
+// Four 32-entry blocks of B from `base` in one round trip (INT_BIG past pd).
+__device__ __forceinline__ void load_b128(const int32_t* __restrict__ B, int pd, int base, int lane, int (&v)[4]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int idx = base + 32 * i + lane;
+        v[i] = idx < pd ? __ldg(B + idx) : INT_BIG;
+    }
+}
+
+// How many of the 128 loaded entries satisfy the (prefix-closed) predicate.
+__device__ __forceinline__ int count_lt(const int (&v)[4], int x) {
+    int n = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) n += __popc(__ballot_sync(FULL, v[i] < x));
+    return n;
+}
+
 // Bit j of the result: entry j of this lane's quad (valid bit j) is in B.
-// Warp-collective; `pos` is the warp's forward cursor into B.
+// Warp-collective; `pos` is the warp's forward cursor into B.  The chunk's
+// window of B usually lies within the 128 entries after the cursor, which
+// one round of loads fetches together with both window bounds.
 __device__ __forceinline__ unsigned chunk_members(const int32_t* __restrict__ B, int pd, int& pos,
                                                   const int (&c)[4], unsigned valid, int lane,
                                                   int* __restrict__ win) {
@@ -265,44 +284,59 @@ __device__ __forceinline__ unsigned chunk_members(const int32_t* __restrict__ B,
     const int amin = __reduce_min_sync(FULL, lmin);
     const int amax = __reduce_max_sync(FULL, lmax);
     if (amin == INT_BIG || pos >= pd) return 0u;
-    const int lo = lower_bound_from(B, pd, pos, amin, lane);
-    int hi = lo;
-    bool big = false;
-    for (;;) {
-        const int idx = hi + lane;
-        const int v = idx < pd ? __ldg(B + idx) : INT_BIG;
-        const int k = __popc(__ballot_sync(FULL, v <= amax));
-        if (hi - lo + k <= WIN) {
-            if (lane < k) win[hi - lo + lane] = v;
-        } else {
-            big = true;
+    int v[4];
+    load_b128(B, pd, pos, lane, v);
+    int nlt = count_lt(v, amin);
+    int lo, hi;
+    bool staged = false;
+    if (nlt == 128) {
+        // the window starts further on: search for it, then load from there
+        lo = lower_bound_from(B, pd, pos + 128, amin, lane);
+        load_b128(B, pd, lo, lane, v);
+        nlt = 0;
+    } else {
+        lo = pos + nlt;
+    }
+    const int base = lo - nlt;  // index of v[0] at lane 0
+    const int nle = amax == INT_BIG - 1 ? 128 : count_lt(v, amax + 1);
+    if (nle < 128) {
+        hi = base + nle;
+        // stage B[lo, hi) (all inside the loaded 128 entries) in shared memory
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = 32 * i + lane;
+            if (e >= nlt && e < nle) win[e - nlt] = v[i];
         }
-        hi += k;
-        if (k < 32) break;
-        if (big) {
-            hi = lower_bound_from(B, pd, hi, amax + 1, lane);
-            break;
-        }
+        staged = true;
+    } else {
+        hi = lower_bound_from(B, pd, base + 128, amax + 1, lane);
     }
     pos = hi;
     const int len = hi - lo;
     if (len == 0) return 0u;
-    __syncwarp();
     unsigned flags = 0;
-    if (!big) {
-        int from = 0;
+    if (staged) {
+        __syncwarp();
+        // this lane's values ascend: one binary search, then short forward steps
+        int a = 0;
+        bool first = true;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             if (!(valid >> j & 1u)) continue;
-            int a = from, b = len;
-            while (a < b) {
-                const int mid = (a + b) >> 1;
-                if (win[mid] < c[j]) a = mid + 1;
-                else b = mid;
+            if (first) {
+                int b = len;
+                while (a < b) {
+                    const int mid = (a + b) >> 1;
+                    if (win[mid] < c[j]) a = mid + 1;
+                    else b = mid;
+                }
+                first = false;
+            } else {
+                while (a < len && win[a] < c[j]) ++a;
             }
             if (a < len && win[a] == c[j]) flags |= 1u << j;
-            from = a;
         }
+        __syncwarp();  // the window is rewritten by the next chunk
     } else {
         int from = lo;
 #pragma unroll
@@ -318,7 +352,6 @@ __device__ __forceinline__ unsigned chunk_members(const int32_t* __restrict__ B,
             from = a;
         }
     }
-    __syncwarp();  // the window is rewritten by the next chunk
     return flags;
 }
 
@@ -871,8 +904,13 @@ struct WarpSmem {
 
 // ------------------------------------------------------------- the engine
 
+// Resident CTAs per SM the register budget is cut for: 24 warps per SM at
+// 256 threads (the engine is latency-bound; occupancy pays more than the
+// few registers it costs).
+constexpr int min_ctas(int nt) { return nt >= 512 ? 1 : (nt >= 256 ? 3 : 6); }
+
 template <int MODE, int NT>
-__global__ void __launch_bounds__(NT) walk_kernel(GraphDev g, const __grid_constant__ ReqTable tab, int n_req,
+__global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, const __grid_constant__ ReqTable tab, int n_req,
                                                   long long total, Scratch* scratch, int sw, int d_t, int seg_q) {
     const ReqDev* __restrict__ reqs = tab.ext ? tab.ext : tab.r;
     __shared__ Smem<NT> sm;
