@@ -37,6 +37,8 @@ WORKLOADS = {
                                   batch_log2=20, slices=1),
     "rmat22_weighted": dict(scale=22, algo="weighted", p=1.0, q=1.0, mode="fast", L=80, types=None,
                             batch_log2=22, slices=1),
+    "rmat25_weighted": dict(scale=25, algo="weighted", p=1.0, q=1.0, mode="fast", L=80, types=None,
+                            batch_log2=22, slices=8),
 }
 
 
@@ -210,6 +212,9 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--threads", type=int, default=0, help="CTA size (0 = library default)")
+    ap.add_argument("--slots", type=int, default=0, help="walk slots per CTA (0 = default)")
+    ap.add_argument("--d-t", type=int, default=0, help="hub threshold d_t (0 = default)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.batch_log2 is not None:
@@ -239,6 +244,8 @@ def main():
     keep_u32 = w["mode"] == "exact"
     dg = DeviceGraph.from_tensors(g.row_ptr, g.col, g.w_f32, g.w_u32 if keep_u32 else None, g.etype,
                                   borrow=True, device=dev)
+    if args.threads or args.slots or args.d_t:
+        dg.set_tuning(block_threads=args.threads, slots=args.slots, d_warp=args.d_t)
     graph_bytes = sum(t.numel() * t.element_size() for t in (g.row_ptr, g.col, g.w_f32))
     batch = 2 ** w["batch_log2"]
     # weak scaling: every rank runs `batch` queries per step, from its own shard

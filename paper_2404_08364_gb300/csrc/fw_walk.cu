@@ -1195,7 +1195,7 @@ cudaError_t launch_one(const GraphDev& g, const ReqTable& reqs, int n_req, int64
     if (need < grid) grid = need > 0 ? need : 1;
     int d_t = tu.d_warp;
     if (MODE == MODE_EXACT) d_t = min(d_t, NCHUNK_MAX * 128 - 8);  // at most NCHUNK_MAX chunks
-    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, reqs, n_req, (long long)total, scratch, sw, d_t, 1024);
+    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, reqs, n_req, (long long)total, scratch, sw, d_t, 4096);
     return cudaGetLastError();
 }
 
