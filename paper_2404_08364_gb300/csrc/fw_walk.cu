@@ -204,6 +204,7 @@ struct WarpPipe {
     unsigned char* buf;
     unsigned long long* bar;
     int* direct;
+    unsigned* mask;  // node2vec membership bits of the current chunk
     int st;
     uint32_t ph;
 };
@@ -355,6 +356,100 @@ __device__ __forceinline__ unsigned chunk_members(const int32_t* __restrict__ B,
     return flags;
 }
 
+// The warp's view of B = N(prev) across the chunks of one step: the 128
+// entries B[base, base + 128) stay loaded in registers (v[i] at lane l is
+// B[base + 32 i + l], INT_BIG past the end) until the chunks move past them.
+struct BBlock {
+    int base;   // -1: nothing loaded yet
+    int v[4];
+};
+
+// node2vec membership for a chunk staged in shared memory, driven from B's
+// side: the chunk's valid entries colS[ia, ib) are sorted, so only the B
+// values inside [colS[ia], colS[ib-1]] can match; each such value (typically
+// a handful per chunk, one per lane) binary-searches the staged chunk and
+// sets its bit in the warp's 128-bit mask.  A chunk whose value range holds
+// more than 256 entries of B (B much denser than this part of N(cur)) is
+// answered from the entries' side instead, by lockstep binary searches of
+// each lane's four values in B.  Returns this lane's four bits (entries
+// 4 lane .. 4 lane + 3 of the chunk).  Warp-collective.
+__device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B, int pd, BBlock& bb,
+                                                const int* __restrict__ colS, int ia, int ib,
+                                                const int c0, const int c1, const int c2, const int c3,
+                                                unsigned valid, int lane, unsigned* __restrict__ mask) {
+    if (ia >= ib || pd == 0) return 0u;
+    const int amin = colS[ia], amax = colS[ib - 1];
+    if (lane < 4) mask[lane] = 0u;
+    __syncwarp();
+    for (int guard = 0; guard < 4; ++guard) {
+        if (bb.base < 0) {
+            bb.base = lower_bound_from(B, pd, 0, amin, lane);
+            load_b128(B, pd, bb.base, lane, bb.v);
+        }
+        int last = __shfl_sync(FULL, bb.v[3], 31);
+        if (last < amin) {
+            // the whole block lies below this chunk: jump to the chunk's range
+            bb.base = lower_bound_from(B, pd, bb.base + 128, amin, lane);
+            load_b128(B, pd, bb.base, lane, bb.v);
+            last = __shfl_sync(FULL, bb.v[3], 31);
+        }
+        if (bb.base >= pd) break;
+        if (last <= amax && guard == 0) {
+            // the chunk's range runs past this block: if B is dense there,
+            // search from the entries' side
+            const int ub = lower_bound_from(B, pd, bb.base + 128, amax == INT_BIG - 1 ? INT_BIG : amax + 1, lane);
+            if (ub - bb.base > 256) {
+                const int lo = bb.base;
+                int a[4], b[4];
+                const int cv[4] = {c0, c1, c2, c3};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    a[j] = lo;
+                    b[j] = (valid >> j & 1u) ? ub : lo;
+                }
+                for (;;) {
+                    bool more = false;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (a[j] < b[j]) {
+                            more = true;
+                            const int mid = (a[j] + b[j]) >> 1;
+                            if (__ldg(B + mid) < cv[j]) a[j] = mid + 1;
+                            else b[j] = mid;
+                        }
+                    if (!more) break;
+                }
+                unsigned f = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if ((valid >> j & 1u) && a[j] < ub && __ldg(B + a[j]) == cv[j]) f |= 1u << j;
+                bb.base = -1;  // the next chunk starts from a fresh search
+                return f;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int bv = bb.v[i];
+            if (bv >= amin && bv <= amax) {
+                int lo = ia, hi = ib;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (colS[mid] < bv) lo = mid + 1;
+                    else hi = mid;
+                }
+                if (lo < ib && colS[lo] == bv) atomicOr(&mask[lo >> 5], 1u << (lo & 31));
+            }
+        }
+        if (last > amax) break;  // the block reaches past the chunk: keep it for the next one
+        // every entry of the block is at most amax: move on to the next block
+        bb.base += 128;
+        if (bb.base >= pd) break;
+        load_b128(B, pd, bb.base, lane, bb.v);
+    }
+    __syncwarp();
+    return (mask[lane >> 3] >> ((lane & 7) * 4)) & 0xFu;
+}
+
 // One lane's four consecutive row entries (an aligned quad of the CSR
 // arrays) with the state-dependent weight of each (0 outside the row).
 template <int MODE>
@@ -422,10 +517,7 @@ __device__ __forceinline__ void load_quad(const GraphDev& g, const StepCtx& cx, 
 // Apply the node2vec factors to a loaded quad (warp-collective: every lane
 // of the warp must call it).
 template <int MODE>
-__device__ __forceinline__ void n2v_apply(const GraphDev& g, const StepCtx& cx, Quad<MODE>& Q, int& pos, int lane,
-                                          int* win) {
-    if (cx.algo != FW_NODE2VEC || cx.prev < 0) return;
-    const unsigned mem = chunk_members(g.col + cx.pbeg, cx.pdeg, pos, Q.c, Q.valid, lane, win);
+__device__ __forceinline__ void n2v_factors(const StepCtx& cx, Quad<MODE>& Q, unsigned mem) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const bool isprev = Q.c[j] == cx.prev;
@@ -433,6 +525,13 @@ __device__ __forceinline__ void n2v_apply(const GraphDev& g, const StepCtx& cx, 
         if (MODE == MODE_EXACT) Q.w[j] *= isprev ? cx.fi0 : (in ? cx.fi1 : cx.fi2);
         else Q.w[j] *= isprev ? cx.ff0 : (in ? cx.ff1 : cx.ff2);
     }
+}
+
+template <int MODE>
+__device__ __forceinline__ void n2v_apply(const GraphDev& g, const StepCtx& cx, Quad<MODE>& Q, int& pos, int lane,
+                                          int* win) {
+    if (cx.algo != FW_NODE2VEC || cx.prev < 0) return;
+    n2v_factors<MODE>(cx, Q, chunk_members(g.col + cx.pbeg, cx.pdeg, pos, Q.c, Q.valid, lane, win));
 }
 
 // A warp's weighted reservoir (exponential race with exponential jumps),
@@ -636,6 +735,9 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
         }
     }
     int pos = 0;
+    BBlock bb;
+    bb.base = -1;
+    const bool n2v = c.algo == FW_NODE2VEC && c.prev >= 0;
     bool ok = true;
     for (int k = 0; k < nch; ++k) {
         const int st = P.st;
@@ -655,13 +757,26 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
         }
         Quad<MODE> cur;
         stage_quad<MODE>(g, c, P, st, qs, qb, end, lane, cur);
-        __syncwarp();  // every lane has its quad: the stage may be refilled
+        if (n2v) {
+            if (P.direct[st]) {
+                n2v_apply<MODE>(g, c, cur, pos, lane, win);
+            } else {
+                // entries [ia, ib) of the staged chunk belong to this row range
+                const long long e0 = qs << 2;
+                const int ia = (int)max(0ll, c.beg - e0);
+                const int ib = (int)min(min((long long)CHQ * 4, end - e0), (qb - qs) << 2);
+                const int* colS = reinterpret_cast<const int*>(P.buf + st * STAGE_BYTES + ST_COL);
+                const unsigned mem = members_staged(g.col + c.pbeg, c.pdeg, bb, colS, ia, ib, cur.c[0], cur.c[1],
+                                                    cur.c[2], cur.c[3], cur.valid, lane, P.mask);
+                n2v_factors<MODE>(c, cur, mem);
+            }
+        }
+        __syncwarp();  // every lane is done with the stage: it may be refilled
         if (lane == 0 && k + NST < nch) {
             const long long qn = qa + (long long)(k + NST) * CHQ;
             pipe_issue<MODE>(g, P, st, qn, (int)min((long long)CHQ, qb - qn), labels);
         }
         ring_next(P.st, P.ph);
-        n2v_apply<MODE>(g, c, cur, pos, lane, win);
         if (MODE == MODE_FAST) {
             const float wf[4] = {(float)cur.w[0], (float)cur.w[1], (float)cur.w[2], (float)cur.w[3]};
             warp_offer_chunk(res, wf, (int)(((qs + lane) << 2) - c.beg), lane, seed, qid, t, rng_stream);
@@ -899,7 +1014,8 @@ struct WarpSmem {
     static constexpr int SUMS_OFF = WIN_OFF + WIN * 4;
     static constexpr int BAR_OFF = SUMS_OFF + (MODE == MODE_EXACT ? NCHUNK_MAX * 8 : 0);
     static constexpr int DIRECT_OFF = BAR_OFF + NST * 8;
-    static constexpr int BYTES = (DIRECT_OFF + NST * 4 + 127) & ~127;
+    static constexpr int MASK_OFF = DIRECT_OFF + NST * 4;
+    static constexpr int BYTES = (MASK_OFF + 16 + 127) & ~127;
 };
 
 // ------------------------------------------------------------- the engine
@@ -925,6 +1041,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
     P.buf = mine;
     P.bar = reinterpret_cast<unsigned long long*>(mine + WarpSmem<MODE>::BAR_OFF);
     P.direct = reinterpret_cast<int*>(mine + WarpSmem<MODE>::DIRECT_OFF);
+    P.mask = reinterpret_cast<unsigned*>(mine + WarpSmem<MODE>::MASK_OFF);
     P.st = 0;
     P.ph = 0;
     if (lane < NST) mbar_init(&P.bar[lane], 1);
