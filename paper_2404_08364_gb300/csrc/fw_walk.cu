@@ -386,6 +386,8 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
             bb.base = lower_bound_from(B, pd, 0, amin, lane);
             load_b128(B, pd, bb.base, lane, bb.v);
         }
+        // (a step normally starts with B's first block already requested by
+        // the caller, overlapping that load with the first chunk's copy)
         int last = __shfl_sync(FULL, bb.v[3], 31);
         if (last < amin) {
             // the whole block lies below this chunk: jump to the chunk's range
@@ -738,6 +740,12 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
     BBlock bb;
     bb.base = -1;
     const bool n2v = c.algo == FW_NODE2VEC && c.prev >= 0;
+    if (n2v && qa == ((c.beg >> 2) & ~3ll)) {
+        // a whole row (or its first segment): start loading N(prev)'s first
+        // block now, while the first chunk is still on its way
+        bb.base = 0;
+        load_b128(g.col + c.pbeg, c.pdeg, 0, lane, bb.v);
+    }
     bool ok = true;
     for (int k = 0; k < nch; ++k) {
         const int st = P.st;
