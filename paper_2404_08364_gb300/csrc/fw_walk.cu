@@ -118,20 +118,6 @@ __device__ __forceinline__ unsigned long long warp_incl_scan_u64(unsigned long l
     return v;
 }
 
-// arg-min over (tau, idx), ties to the smaller index; idx < 0 means "none".
-__device__ __forceinline__ void warp_argmin(float& tau, int& idx) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float t2 = __shfl_xor_sync(FULL, tau, o);
-        const int i2 = __shfl_xor_sync(FULL, idx, o);
-        const bool take = (i2 >= 0) && (idx < 0 || t2 < tau || (t2 == tau && i2 < idx));
-        if (take) {
-            tau = t2;
-            idx = i2;
-        }
-    }
-}
-
 __device__ __forceinline__ float unit_open(uint32_t w) {
     // strictly inside (0, 1): 23 random bits centred in their cell, so the
     // largest value is 1 - 2^-24 (exact in FP32) and -log(u) > 0 always
@@ -1075,6 +1061,8 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
         long long qa, qb;
         uint64_t seed, qid;
         uint32_t t, stream;
+        int nunits = 1;          // segments this warp samples in a row (1, or a hub
+        long long unit_q = 0;    // task's segments when no task entry was free)
         unsigned long long* sums = nullptr;
         int h, j;
         int s = -1;
@@ -1243,6 +1231,15 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                 hh = __shfl_sync(FULL, hh, 0);
                 if (hh >= 0) continue;   // the walk waits for the CTA sampler; go on with other work
                 if (too_long) continue;  // no free entry: retry after helping the open ones
+                if (MODE == MODE_FAST) {
+                    // no free entry: this warp samples the hub task's segments
+                    // itself, with the same random streams, so the result does
+                    // not depend on who did the work
+                    const long long nq = qb - qa;
+                    long long sq = max((long long)seg_q, (nq + NSEG_MAX - 1) / NSEG_MAX);
+                    unit_q = (sq + 31) & ~31ll;
+                    nunits = (int)((nq + unit_q - 1) / unit_q);
+                }
             }
             stream = 0;
             if (MODE == MODE_EXACT) sums = chunk_sums;
@@ -1251,10 +1248,24 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
 
         // ------------------------------------ stream the row range (one site)
         WarpRes res;
-        res.init();
         unsigned long long lane_sum = 0;
         const long long end = c.beg + c.d;
-        if (!scan_range<MODE>(g, c, qa, qb, end, lane, win, P, res, lane_sum, sums, stream, seed, qid, t)) {
+        if (nunits == 1) unit_q = qb - qa;
+        float best_tau = __int_as_float(0x7f800000);
+        int best_sel = -1;
+        bool ok = true;
+        for (int u = 0; u < nunits && ok; ++u) {
+            const long long ua = qa + (long long)u * unit_q, ub = min(qb, ua + unit_q);
+            res.init();
+            ok = scan_range<MODE>(g, c, ua, ub, end, lane, win, P, res, lane_sum, sums,
+                                  nunits > 1 ? (uint32_t)u : stream, seed, qid, t);
+            // merge segments like the hub task does: smaller race time, then smaller index
+            if (res.sel >= 0 && (best_sel < 0 || res.tau < best_tau || (res.tau == best_tau && res.sel < best_sel))) {
+                best_tau = res.tau;
+                best_sel = res.sel;
+            }
+        }
+        if (!ok) {
             if (lane == 0) atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
             break;
         }
@@ -1267,7 +1278,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
         int sel = -1;
         uint32_t oz = 0xFFFFFFFFu;
         if (MODE == MODE_FAST) {
-            sel = res.sel;
+            sel = best_sel;
             if (sel >= 0 && R->algo == FW_PPR) oz = step_block(seed, qid, t).z;
         } else {
             const unsigned long long W = warp_sum_u64(lane_sum);
@@ -1289,7 +1300,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
             if (sel < 0) {
                 sm.state[s] = ST_FINISH;  // nothing selectable: the walk stops here
             } else {
-                cnt.step(c.d, c.algo, false);
+                cnt.step(c.d, c.algo, nunits > 1);
                 commit(g, sm, *R, s, c, __ldg(g.col + c.beg + sel), oz);
             }
         }
