@@ -196,6 +196,33 @@ typedef struct {
  */
 int fw_walk_multi(fw_graph* g, const fw_request* reqs, int32_t n_req, void* stream);
 
+/*
+ * fw_walk_noalloc — the multi-request launch of fw_walk_multi for callers
+ * that must not allocate device memory at call time: code that runs while a
+ * latency-critical server loop holds the device (a cudaMalloc there can
+ * synchronise the whole device), callers whose allocator owns all device
+ * memory, and callers in environments that forbid runtime allocation.  The
+ * paper has no counterpart; this is a deployment convenience.
+ *
+ *   g, reqs, n_req, stream   as fw_walk_multi; every buffer is device memory
+ *                            the caller owns; 1 <= n_req <= FW_NOALLOC_MAX_REQS.
+ * Scratch: the request table, the query cursor and the counters of the launch
+ * live in one static device array compiled into the library (about
+ * FW_NOALLOC_MAX_REQS × 168 bytes + 128 bytes), which every GPU that loads the
+ * library holds until the process exits.  Nothing is allocated: no cudaMalloc,
+ * no cudaFree, no host heap.  The first call on a device looks the array's
+ * device address up (cudaGetSymbolAddress) with that device current: make that
+ * first call before any stream capture.  The array is shared by all calls and
+ * keeps the last call's contents; each call resets the cursor and counters it
+ * uses.  Two calls whose launches overlap on the GPU (different streams, no
+ * ordering between them) race on the array: order them on one stream.  Counts
+ * of these launches do not appear in fw_stats.
+ * Errors: FW_EINVAL (n_req outside [1, FW_NOALLOC_MAX_REQS], host buffers,
+ * bad parameters), FW_ECUDA.
+ */
+#define FW_NOALLOC_MAX_REQS 1024
+int fw_walk_noalloc(fw_graph* g, const fw_request* reqs, int32_t n_req, void* stream);
+
 /* Same as fw_walk with an explicit query-id offset q_id0 (for sharding one
  * query range over several calls or devices with identical results). */
 int fw_walk_ex(fw_graph* g, int32_t algo, const fw_params* p, const int32_t* starts, int64_t n_q,

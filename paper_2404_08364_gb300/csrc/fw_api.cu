@@ -580,3 +580,89 @@ extern "C" int fw_philox(const uint32_t* in, uint32_t* out, int64_t n, void* str
     FW_CUDA_TRY(cudaGetLastError());
     return FW_OK;
 }
+
+// ------------------------------------------------------ no-allocation launch
+//
+// For callers that cannot allocate device memory when they walk: the request
+// table, query cursor and counters of the launch live in this one file-scope
+// device array instead of graph-owned or freshly allocated memory.  Host code
+// may not pass the symbol itself to a kernel (in host code it names a host
+// stand-in), so its device address is looked up once per device.
+
+namespace {
+struct NoAllocScratch {
+    Scratch s;                          // cursor + counters (reset every call)
+    ReqDev reqs[FW_NOALLOC_MAX_REQS];   // the launch's request table
+};
+}  // namespace
+
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+namespace {
+std::mutex g_noalloc_mu;
+constexpr int kMaxDevices = 64;
+NoAllocScratch* g_noalloc_addr[kMaxDevices];  // device address per device, looked up once
+ReqDev g_noalloc_host[FW_NOALLOC_MAX_REQS];   // host staging of the table (under the mutex)
+}  // namespace
+
+extern "C" int fw_walk_noalloc(fw_graph* G, const fw_request* reqs, int32_t n_req, void* stream) {
+    if (!G || !reqs) return fail(FW_EINVAL, "fw_walk_noalloc: NULL argument");
+    if (n_req < 1 || n_req > FW_NOALLOC_MAX_REQS)
+        return fail(FW_EINVAL, "fw_walk_noalloc: n_req = %d, must be in [1, %d]", n_req, FW_NOALLOC_MAX_REQS);
+    if (G->device < 0 || G->device >= kMaxDevices) return fail(FW_EINVAL, "fw_walk_noalloc: device ordinal too large");
+    std::lock_guard<std::mutex> glock(G->mu);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    int cur_dev = 0;
+    cudaGetDevice(&cur_dev);
+    if (cur_dev != G->device) FW_CUDA_TRY(cudaSetDevice(G->device));
+    struct DevGuard {
+        int d;
+        ~DevGuard() { cudaSetDevice(d); }
+    } guard{cur_dev};
+    NoAllocScratch* dev = g_noalloc_addr[G->device];
+    if (!dev) {
+        // set-up, once per device, with that device current
+        cudaError_t e = cudaGetSymbolAddress((void**)&dev, g_noalloc_scratch);
+        if (e != cudaSuccess || !dev)
+            return fail(FW_ECUDA, "fw_walk_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_noalloc_addr[G->device] = dev;
+    }
+    int64_t total = 0;
+    const int mode = reqs[0].params.mode;
+    for (int i = 0; i < n_req; ++i) {
+        const fw_request& q = reqs[i];
+        if (q.params.mode != mode) return fail(FW_EINVAL, "fw_walk_noalloc: requests must share one mode");
+        if (q.n_q < 0) return fail(FW_EINVAL, "fw_walk_noalloc: n_q < 0");
+        if (q.n_q > 0 && (!q.starts || !q.paths || !q.path_len))
+            return fail(FW_EINVAL, "fw_walk_noalloc: NULL starts/paths/path_len");
+        const void* ps[] = {q.starts, q.lengths, q.prev, q.step0, q.paths, q.path_len};
+        for (const void* pp : ps)
+            if (pp && !is_device_ptr(pp)) return fail(FW_EINVAL, "fw_walk_noalloc: buffers must be device memory");
+        ReqDev& r = g_noalloc_host[i];
+        int rc = make_req(G, q.algo, &q.params, q.max_len, q.seed, &r);
+        if (rc != FW_OK) return rc;
+        r.starts = q.starts;
+        r.lengths = q.lengths;
+        r.prev = q.prev;
+        r.step0 = q.step0;
+        r.paths = q.paths;
+        r.path_len = q.path_len;
+        r.n_q = q.n_q;
+        r.q_begin = total;
+        r.q_id0 = q.q_id0;
+        total += q.n_q;
+    }
+    if (total == 0) return FW_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the table comes from pageable host memory: the copy has taken the data
+    // by the time cudaMemcpyAsync returns, so the staging array may be reused
+    FW_CUDA_TRY(cudaMemcpyAsync(dev->reqs, g_noalloc_host, sizeof(ReqDev) * (size_t)n_req,
+                                cudaMemcpyHostToDevice, st));
+    FW_CUDA_TRY(cudaMemsetAsync(&dev->s, 0, sizeof(Scratch), st));  // the cursor must start at zero
+    ReqTable tab;
+    memset(&tab, 0, sizeof tab);
+    tab.ext = dev->reqs;
+    cudaError_t e = launch_walk(G->g, mode, tab, n_req, total, &dev->s, G->tuning, st);
+    if (e != cudaSuccess) return fail(FW_ECUDA, "fw_walk_noalloc: launch: %s", cudaGetErrorString(e));
+    return FW_OK;
+}

@@ -97,6 +97,43 @@ class DeviceGraph:
                                        _ptr(path_len), sh))
         return paths, path_len
 
+    def _requests(self, requests):
+        arr = (_fw.Request * len(requests))()
+        outs, keep = [], []
+        for i, r in enumerate(requests):
+            st = _i32(r["starts"], "cuda")
+            n_q = st.numel()
+            L = int(r["max_len"])
+            paths = r.get("paths")
+            if paths is None:
+                paths = torch.empty((n_q, L + 1), dtype=torch.int32, device=st.device)
+            plen = r.get("path_len")
+            if plen is None:
+                plen = torch.empty(n_q, dtype=torch.int32, device=st.device)
+            ln, pv, s0 = (_i32(r.get(k), st.device) for k in ("lengths", "prev", "step0"))
+            keep += [st, ln, pv, s0]
+            q = arr[i]
+            q.algo = _fw.ALGOS.get(r["algo"], r["algo"])
+            q.params = _fw.make_params(r.get("mode", "exact"), r.get("p", 1.0), r.get("q", 1.0),
+                                       r.get("scale", 2), r.get("schema", (0, 1, 2, 3, 4)),
+                                       r.get("ppr_stop", 0.2))
+            q.starts, q.n_q, q.max_len = st.data_ptr(), n_q, L
+            q.lengths = ln.data_ptr() if ln is not None else None
+            q.prev = pv.data_ptr() if pv is not None else None
+            q.step0 = s0.data_ptr() if s0 is not None else None
+            q.seed = int(r["seed"]) & 0xFFFFFFFFFFFFFFFF
+            q.q_id0 = int(r.get("q_id0", 0))
+            q.paths, q.path_len = paths.data_ptr(), plen.data_ptr()
+            outs.append((paths, plen))
+        return arr, outs, keep
+
+    def walk_noalloc(self, requests, stream=None):
+        """Like walk_multi, through fw_walk_noalloc: the library allocates no
+        device memory for the launch (up to 1024 requests, device tensors)."""
+        arr, outs, keep = self._requests(requests)
+        _fw.check(_fw.lib().fw_walk_noalloc(self._h, arr, len(requests), _stream_handle(stream)))
+        return outs
+
     def walk_multi(self, requests, stream=None):
         """requests: list of dicts with keys algo, starts, max_len, seed, mode,
         p, q, scale, schema, ppr_stop, lengths, prev, step0, q_id0, paths,
