@@ -230,6 +230,76 @@ int fw_walk_ex(fw_graph* g, int32_t algo, const fw_params* p, const int32_t* sta
                const int32_t* prev, const int32_t* step0, int32_t* paths, int32_t* path_len,
                void* stream);
 
+/*
+ * Served form: continuous batching on a resident graph.
+ *
+ * A server owns a device output arena of mem_budget bytes and a ring of up to
+ * max_requests live requests.  fw_server_submit copies a request's inputs
+ * (host starts / lengths / prev / step0) and queues it; a server thread
+ * admits queued requests in arrival order as soon as the arena has room for
+ * their outputs (admission by output-buffer memory) and publishes them to the
+ * running engine, whose warps pick them up between steps of the walks already
+ * on the GPU (no batch barrier).  When a request's last walk ends its paths
+ * and path_len are copied to the request's HOST buffers (paths, path_len,
+ * which must stay valid until then) and its arena space is freed.
+ *   mode         FW_EXACT or FW_FAST for every request of this server.
+ *   idle_ms      the engine returns after this long without work and is
+ *                relaunched when work arrives (<= 0: 20 ms).
+ * A request's random counters use its own seed and its own query ids
+ * (q_id0 + i), so its paths equal those of the same request run alone
+ * (bit for bit in exact mode; in fast mode for the same engine tuning).
+ * Latency = submission to outputs in the caller's buffers.
+ * Errors: FW_EINVAL (arguments, mode mismatch, start out of range), FW_EBUSY
+ * (a request larger than the whole arena), FW_ETIMEOUT (wait), FW_ENOMEM,
+ * FW_ECUDA.
+ */
+typedef struct fw_server fw_server;
+
+typedef struct {
+    uint64_t completed;      /* requests finished */
+    uint64_t steps;          /* moves of the finished requests */
+    uint64_t launches;       /* engine launches (relaunches after idle) */
+    uint64_t pending;        /* requests waiting for admission */
+    uint64_t arena_used;     /* bytes of the output arena in use */
+    uint64_t arena_capacity;
+    double busy_s;           /* first submission to last completion */
+} fw_server_stats_t;
+
+int fw_server_create(fw_graph* g, int32_t mode, uint64_t mem_budget, int32_t max_requests, double idle_ms,
+                     fw_server** out);
+int fw_server_submit(fw_server* s, const fw_request* req, uint64_t* ticket);
+int fw_server_poll(fw_server* s, uint64_t ticket, int32_t* done, double* latency_s);
+int fw_server_wait(fw_server* s, uint64_t ticket, double timeout_s, double* latency_s);
+int fw_server_release(fw_server* s, uint64_t ticket);
+int fw_server_stats(fw_server* s, fw_server_stats_t* out);
+void fw_server_destroy(fw_server* s);
+
+/*
+ * CUDA-graph form of a multi-request launch: fw_capture_multi records the
+ * cursor reset and the persistent engine launch of fw_walk_multi(reqs) into
+ * a CUDA graph; fw_exec_launch replays it on `stream` (the same buffers: the
+ * caller may rewrite starts, lengths, prev and step0 in place between
+ * replays).  Device buffers only; errors as fw_walk_multi, FW_ECUDA.
+ */
+typedef struct fw_exec fw_exec;
+int fw_capture_multi(fw_graph* g, const fw_request* reqs, int32_t n_req, fw_exec** out);
+int fw_exec_launch(fw_exec* x, void* stream);
+void fw_exec_destroy(fw_exec* x);
+
+/*
+ * Engine autotuner (Section 5.1's |P_L| and d_t, and the CTA size): runs
+ * fw_walk_multi(reqs) — a representative sample of the workload, device
+ * buffers — over a grid of tunings (128/256/512 threads, d_t 2^11 .. 2^20,
+ * 1..4 walk slots per warp), `reps` timed launches each, keeps the fastest in
+ * walk steps per second, sets it on g and returns it in *best (and its rate in
+ * *best_steps_per_s when not NULL).  The choice is cached by (GPU name,
+ * algorithms and mode of the sample, log2 mean and max degree of g); a cache
+ * hit returns at once with rate 0.  1 <= n_req <= 16.
+ */
+int fw_autotune(fw_graph* g, const fw_request* reqs, int32_t n_req, int32_t reps, fw_tuning* best,
+                double* best_steps_per_s);
+int fw_autotune_clear_cache(void);
+
 /* Set / get the engine tuning used by later walks on g (NULL = defaults). */
 int fw_set_tuning(fw_graph* g, const fw_tuning* t);
 int fw_get_tuning(const fw_graph* g, fw_tuning* out);

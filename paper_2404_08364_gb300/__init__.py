@@ -6,7 +6,7 @@ binding.  Importing the package does not load the library; the first use of
 ``DeviceGraph`` does, and raises if it is missing.
 """
 
-__all__ = ["DeviceGraph", "build"]
+__all__ = ["DeviceGraph", "Server", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -15,7 +15,7 @@ def build(force: bool = False) -> str:
 
 
 def __getattr__(name):
-    if name == "DeviceGraph":
-        from .walker import DeviceGraph
-        return DeviceGraph
+    if name in ("DeviceGraph", "Server"):
+        from . import walker
+        return getattr(walker, name)
     raise AttributeError(name)

@@ -55,6 +55,12 @@ class Request(ctypes.Structure):
                 ("step0", ctypes.c_void_p), ("paths", ctypes.c_void_p), ("path_len", ctypes.c_void_p)]
 
 
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("steps", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("pending", ctypes.c_uint64), ("arena_used", ctypes.c_uint64),
+                ("arena_capacity", ctypes.c_uint64), ("busy_s", ctypes.c_double)]
+
+
 # exported symbol -> (restype, argtypes)
 _P = ctypes.c_void_p
 SIGNATURES = {
@@ -76,6 +82,21 @@ SIGNATURES = {
                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]),
     "fw_philox": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "fw_server_create": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double,
+                                        ctypes.POINTER(_P)]),
+    "fw_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]),
+    "fw_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "fw_server_wait": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]),
+    "fw_server_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "fw_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "fw_server_destroy": (None, [_P]),
+    "fw_capture_multi": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.c_int32, ctypes.POINTER(_P)]),
+    "fw_exec_launch": (ctypes.c_int, [_P, _P]),
+    "fw_exec_destroy": (None, [_P]),
+    "fw_autotune": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.c_int32, ctypes.c_int32,
+                                   ctypes.POINTER(Tuning), ctypes.POINTER(ctypes.c_double)]),
+    "fw_autotune_clear_cache": (ctypes.c_int, []),
     "fw_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "fw_last_error": (ctypes.c_char_p, []),
     "fw_version": (ctypes.c_int, []),

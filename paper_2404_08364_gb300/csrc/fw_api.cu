@@ -376,6 +376,23 @@ int launch(fw_graph* G, int mode, const ReqTable& tab, int n_req, int64_t total,
 
 }  // namespace
 
+namespace fw {
+
+int set_error(int status, const char* msg) { return fail(status, "%s", msg); }
+
+int graph_device_view(const fw_graph* g, GraphDev* out, int* device, Tuning* tuning) {
+    *out = g->g;
+    *device = g->device;
+    *tuning = g->tuning;
+    return FW_OK;
+}
+
+int make_request(const fw_graph* g, const fw_request& q, ReqDev* out) {
+    return make_req(g, q.algo, &q.params, q.max_len, q.seed, out);
+}
+
+}  // namespace fw
+
 extern "C" int fw_walk_ex(fw_graph* G, int32_t algo, const fw_params* p, const int32_t* starts, int64_t n_q,
                           const int32_t* lengths, int32_t max_len, uint64_t seed, int64_t q_id0,
                           const int32_t* prev, const int32_t* step0, int32_t* paths, int32_t* path_len,

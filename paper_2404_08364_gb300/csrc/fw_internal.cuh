@@ -120,6 +120,22 @@ struct ReqTable {
     ReqDev r[kMaxInlineReqs];
 };
 
+// Served form: requests live in a device ring that the host keeps extending
+// while the kernel runs; the kernel claims published queries, and the last
+// walk of a request stamps its completion word in host memory.  All waits on
+// the host words are bounded by idle_ns.
+struct ServeDev {
+    ReqDev* ring;                                 // device, maxr entries (null: batch launch)
+    int maxr;
+    unsigned long long* done;                     // device, per ring slot: walks retired
+    unsigned long long* cursor;                   // device: next query to hand out
+    const volatile unsigned long long* pub_q;     // mapped host: queries published so far
+    const volatile unsigned long long* pub_r;     // mapped host: requests published so far
+    const volatile int* stop;                     // mapped host: drain and return
+    volatile unsigned long long* complete;        // mapped host: per ring slot, nonzero when done
+    unsigned long long idle_ns;                   // return after this long without any work
+};
+
 struct Tuning {
     int block_threads;
     int slots;
@@ -132,7 +148,17 @@ struct Tuning {
 cudaError_t launch_walk(const GraphDev& g, int mode, const ReqTable& reqs, int n_req, int64_t total,
                         Scratch* scratch, const Tuning& tune, cudaStream_t stream);
 
+// Launch the engine in served mode (runs until stopped or idle).  Defined in
+// fw_walk.cu.
+cudaError_t launch_serve(const GraphDev& g, int mode, const ServeDev& sv, Scratch* scratch, const Tuning& tune,
+                         cudaStream_t stream);
+
 Tuning default_tuning();
 Tuning sanitize_tuning(Tuning t);
+
+// Library-internal helpers shared by the ABI translation units (fw_api.cu).
+int set_error(int status, const char* msg);                          // records the message, returns status
+int graph_device_view(const fw_graph* g, GraphDev* out, int* device, Tuning* tuning);
+int make_request(const fw_graph* g, const fw_request& q, ReqDev* out);  // parameters only
 
 }  // namespace fw

@@ -34,6 +34,7 @@
 // four entries, 16-byte loads of columns and weights), with the next chunk's
 // loads in flight while the current one is sampled.
 #include <math.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -365,6 +366,15 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
                                                 unsigned valid, int lane, unsigned* __restrict__ mask) {
     if (ia >= ib || pd == 0) return 0u;
     const int amin = colS[ia], amax = colS[ib - 1];
+    if (bb.base >= 0) {
+        // common case: the loaded block reaches past this chunk and holds no
+        // value inside its range: nothing can match, one vote decides it
+        const int last = __shfl_sync(FULL, bb.v[3], 31);
+        bool in = false;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) in |= bb.v[i] >= amin && bb.v[i] <= amax;
+        if (last > amax && !__any_sync(FULL, in)) return 0u;
+    }
     if (lane < 4) mask[lane] = 0u;
     __syncwarp();
     for (int guard = 0; guard < 4; ++guard) {
@@ -843,6 +853,20 @@ __device__ __forceinline__ int find_req(const ReqDev* __restrict__ reqs, int n_r
     return lo;
 }
 
+// Served form: the ring slot of the request holding query gq.  Requests are
+// published in order with ascending q_begin; the live window is the last
+// maxr requests.
+__device__ __forceinline__ int find_ring(const ServeDev& sv, long long gq) {
+    const long long R = (long long)*sv.pub_r;
+    long long lo = R > sv.maxr ? R - sv.maxr : 0, hi = R - 1;
+    while (lo < hi) {
+        const long long mid = (lo + hi + 1) >> 1;
+        if (sv.ring[mid % sv.maxr].q_begin <= gq) lo = mid;
+        else hi = mid - 1;
+    }
+    return (int)(lo % sv.maxr);
+}
+
 // Per-warp counters, kept by lane 0 and flushed at exit.
 struct Counters {
     unsigned long long v[C_NUM];
@@ -1021,8 +1045,10 @@ constexpr int min_ctas(int nt) { return nt >= 512 ? 1 : (nt >= 256 ? 3 : 6); }
 
 template <int MODE, int NT>
 __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, const __grid_constant__ ReqTable tab, int n_req,
-                                                  long long total, Scratch* scratch, int sw, int d_t, int seg_q) {
-    const ReqDev* __restrict__ reqs = tab.ext ? tab.ext : tab.r;
+                                                  long long total, Scratch* scratch, int sw, int d_t, int seg_q,
+                                                  ServeDev sv) {
+    const bool serving = sv.ring != nullptr;
+    const ReqDev* __restrict__ reqs = serving ? sv.ring : (tab.ext ? tab.ext : tab.r);
     __shared__ Smem<NT> sm;
     // dynamic shared memory per warp: the node2vec window (WIN ints) and, in
     // exact mode, the warp sampler's chunk sums
@@ -1089,12 +1115,30 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                 if (st == ST_EMPTY && !exhausted) {
                     // claim one query (lane 0) and initialise the slot
                     long long gq = 0;
-                    if (lane == 0) gq = (long long)atomicAdd(&scratch->cursor, 1ull);
-                    gq = __shfl_sync(FULL, gq, 0);
-                    if (gq >= total) {
-                        exhausted = true;
-                    } else if (lane == 0) {
-                        const int r = find_req(reqs, n_req, gq);
+                    int r = 0;
+                    if (serving) {
+                        // served form: take the next published query, if any
+                        gq = -1;
+                        if (lane == 0) {
+                            for (int tries = 0; tries < 64; ++tries) {
+                                const unsigned long long cq = *(volatile unsigned long long*)sv.cursor;
+                                if (cq >= *sv.pub_q) break;
+                                if (atomicCAS(sv.cursor, cq, cq + 1) == cq) {
+                                    gq = (long long)cq;
+                                    r = find_ring(sv, gq);
+                                    break;
+                                }
+                            }
+                        }
+                        gq = __shfl_sync(FULL, gq, 0);
+                        if (gq < 0) continue;  // nothing published right now: the slot stays empty
+                    } else {
+                        if (lane == 0) gq = (long long)atomicAdd(&scratch->cursor, 1ull);
+                        gq = __shfl_sync(FULL, gq, 0);
+                        if (gq >= total) exhausted = true;
+                        else if (lane == 0) r = find_req(reqs, n_req, gq);
+                    }
+                    if (!exhausted && lane == 0) {
                         const ReqDev& Rq = reqs[r];
                         const long long qi = gq - Rq.q_begin;
                         const int start = __ldg(Rq.starts + qi);
@@ -1141,6 +1185,16 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                         Rq.path_len[sm.q[jj]] = k;
                         cnt.v[C_WALKS] += 1;
                         sm.state[jj] = ST_EMPTY;
+                        if (serving) {
+                            // the request's last walk tells the host (all its
+                            // writes are visible first)
+                            __threadfence();
+                            const int rs = sm.req[jj];
+                            if (atomicAdd(&sv.done[rs], 1ull) + 1 == (unsigned long long)Rq.n_q) {
+                                __threadfence_system();
+                                sv.complete[rs] = global_timer_ns() | 1ull;
+                            }
+                        }
                     }
                     __syncwarp();
                     --i;  // revisit this slot: it can be refilled now
@@ -1152,6 +1206,20 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                     rr = (jj - s0 + 1) % sw;
                     break;
                 }
+            }
+            if (s < 0 && !waiting && serving) {
+                // served form with nothing to do: wait for new requests, bounded
+                const unsigned long long now = global_timer_ns();
+                int quit = 0;
+                if (lane == 0) {
+                    if (*sv.stop) quit = 1;
+                    else if (idle_since == 0) idle_since = now;
+                    else if (now - idle_since > sv.idle_ns) quit = 1;
+                }
+                if (__shfl_sync(FULL, quit, 0)) break;
+                idle_since = __shfl_sync(FULL, idle_since, 0);
+                __nanosleep(2000);
+                continue;
             }
             if (s < 0) {
                 if (!waiting) break;  // all slots empty and no more queries
@@ -1331,13 +1399,38 @@ cudaError_t launch_one(const GraphDev& g, const ReqTable& reqs, int n_req, int64
     if (need < grid) grid = need > 0 ? need : 1;
     int d_t = tu.d_warp;
     if (MODE == MODE_EXACT) d_t = min(d_t, NCHUNK_MAX * 128 - 8);  // at most NCHUNK_MAX chunks
-    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, reqs, n_req, (long long)total, scratch, sw, d_t, 4096);
+    ServeDev none;
+    memset(&none, 0, sizeof none);
+    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, reqs, n_req, (long long)total, scratch, sw, d_t, 4096, none);
+    return cudaGetLastError();
+}
+
+template <int MODE, int NT>
+cudaError_t launch_serve_one(const GraphDev& g, const ServeDev& sv, Scratch* scratch, const Tuning& tu,
+                             cudaStream_t stream) {
+    auto kern = walk_kernel<MODE, NT>;
+    const size_t dyn = (size_t)(NT / 32) * WarpSmem<MODE>::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, dyn);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (tu.ctas_per_sm > 0) per_sm = min(per_sm, tu.ctas_per_sm);
+    const int sw = max(1, min(SW_MAX, tu.slots / (NT / 32)));
+    int d_t = tu.d_warp;
+    if (MODE == MODE_EXACT) d_t = min(d_t, NCHUNK_MAX * 128 - 8);
+    ReqTable tab;
+    memset(&tab, 0, sizeof tab);
+    kern<<<(unsigned)(sms * per_sm), NT, dyn, stream>>>(g, tab, 0, 0ll, scratch, sw, d_t, 4096, sv);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-Tuning default_tuning() { return Tuning{256, 16, 8192, 0}; }
+Tuning default_tuning() { return Tuning{256, 16, 16384, 0}; }
 
 Tuning sanitize_tuning(Tuning t) {
     const Tuning d = default_tuning();
@@ -1349,6 +1442,23 @@ Tuning sanitize_tuning(Tuning t) {
     if (t.d_warp > (1 << 30)) t.d_warp = 1 << 30;
     if (t.ctas_per_sm < 0) t.ctas_per_sm = 0;
     return t;
+}
+
+cudaError_t launch_serve(const GraphDev& g, int mode, const ServeDev& sv, Scratch* scratch, const Tuning& tune,
+                         cudaStream_t stream) {
+    const Tuning tu = sanitize_tuning(tune);
+    const bool exact = mode == FW_EXACT;
+    switch (tu.block_threads) {
+        case 128:
+            return exact ? launch_serve_one<MODE_EXACT, 128>(g, sv, scratch, tu, stream)
+                         : launch_serve_one<MODE_FAST, 128>(g, sv, scratch, tu, stream);
+        case 512:
+            return exact ? launch_serve_one<MODE_EXACT, 512>(g, sv, scratch, tu, stream)
+                         : launch_serve_one<MODE_FAST, 512>(g, sv, scratch, tu, stream);
+        default:
+            return exact ? launch_serve_one<MODE_EXACT, 256>(g, sv, scratch, tu, stream)
+                         : launch_serve_one<MODE_FAST, 256>(g, sv, scratch, tu, stream);
+    }
 }
 
 cudaError_t launch_walk(const GraphDev& g, int mode, const ReqTable& reqs, int n_req, int64_t total,

@@ -169,6 +169,25 @@ class DeviceGraph:
         _fw.check(_fw.lib().fw_walk_multi(self._h, arr, len(requests), _stream_handle(stream)))
         return outs
 
+    def capture_multi(self, requests) -> "Exec":
+        """Record the multi-request launch into a CUDA graph (fw_capture_multi);
+        replay it with Exec.launch().  The request tensors stay attached to it."""
+        arr, outs, keep = self._requests(requests)
+        h = _P()
+        _fw.check(_fw.lib().fw_capture_multi(self._h, arr, len(requests), ctypes.byref(h)))
+        return Exec(h, outs, keep)
+
+    def autotune(self, requests, reps: int = 2) -> dict:
+        """Pick the engine tuning on a sample workload (fw_autotune); returns it
+        with the measured steps/s (0 on a cache hit)."""
+        arr, outs, keep = self._requests(requests)
+        t = _fw.Tuning()
+        rate = ctypes.c_double()
+        _fw.check(_fw.lib().fw_autotune(self._h, arr, len(requests), int(reps), ctypes.byref(t), ctypes.byref(rate)))
+        d = {k: getattr(t, k) for k, _ in _fw.Tuning._fields_}
+        d["steps_per_s"] = rate.value
+        return d
+
     # ------------------------------------------------------------ management
     def set_tuning(self, block_threads=0, slots=0, d_warp=0, ctas_per_sm=0):
         t = _fw.Tuning(block_threads, slots, d_warp, ctas_per_sm)
@@ -203,5 +222,102 @@ class DeviceGraph:
     def __del__(self):
         try:
             self.free()
+        except Exception:
+            pass
+
+
+class Exec:
+    """A captured multi-request launch (CUDA graph)."""
+
+    def __init__(self, handle, outs, keep):
+        self._h = handle
+        self.outputs = outs
+        self._keep = keep
+
+    def launch(self, stream=None):
+        _fw.check(_fw.lib().fw_exec_launch(self._h, _stream_handle(stream)))
+        return self.outputs
+
+    def close(self):
+        if self._h:
+            _fw.lib().fw_exec_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Served form (fw_server_*): a resident graph, requests admitted by
+    output-arena memory and run by the persistent engine as they arrive.
+
+        srv = Server(dg, mode="fast", mem_budget=1 << 30)
+        t = srv.submit("node2vec", starts_cpu, max_len=80, seed=7, p=2, q=0.5)
+        paths, plen, latency_s = srv.result(t)
+    """
+
+    def __init__(self, graph: DeviceGraph, mode="fast", mem_budget: int = 1 << 30, max_requests: int = 1024,
+                 idle_ms: float = 20.0):
+        self._g = graph
+        self.mode = _fw.MODES.get(mode, mode)
+        h = _P()
+        _fw.check(_fw.lib().fw_server_create(graph._h, self.mode, int(mem_budget), int(max_requests),
+                                             float(idle_ms), ctypes.byref(h)))
+        self._h = h
+        self._out = {}
+
+    def submit(self, algo, starts, max_len: int, seed: int, p=1.0, q=1.0, scale=2,
+               schema: Sequence[int] = (0, 1, 2, 3, 4), ppr_stop=0.2, lengths=None, prev=None, step0=None,
+               q_id0: int = 0) -> int:
+        """Queue one request (host tensors); returns its ticket."""
+        st = _i32(starts, "cpu")
+        n_q = st.numel()
+        paths = torch.empty((n_q, max_len + 1), dtype=torch.int32).pin_memory()
+        plen = torch.empty(n_q, dtype=torch.int32).pin_memory()
+        ln, pv, s0 = _i32(lengths, "cpu"), _i32(prev, "cpu"), _i32(step0, "cpu")
+        r = _fw.Request()
+        r.algo = _fw.ALGOS.get(algo, algo)
+        r.params = _fw.make_params(self.mode, p, q, scale, schema, ppr_stop)
+        r.starts, r.n_q, r.max_len = st.data_ptr(), n_q, int(max_len)
+        r.lengths = ln.data_ptr() if ln is not None else None
+        r.prev = pv.data_ptr() if pv is not None else None
+        r.step0 = s0.data_ptr() if s0 is not None else None
+        r.seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+        r.q_id0 = int(q_id0)
+        r.paths, r.path_len = paths.data_ptr(), plen.data_ptr()
+        t = ctypes.c_uint64()
+        _fw.check(_fw.lib().fw_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        self._out[t.value] = (paths, plen)
+        return t.value
+
+    def poll(self, ticket: int):
+        done, lat = ctypes.c_int32(), ctypes.c_double()
+        _fw.check(_fw.lib().fw_server_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(lat)))
+        return done.value, lat.value
+
+    def result(self, ticket: int, timeout_s: float = 120.0):
+        """Wait for a ticket; returns (paths, path_len, latency_s) and forgets it."""
+        lat = ctypes.c_double()
+        _fw.check(_fw.lib().fw_server_wait(self._h, ticket, float(timeout_s), ctypes.byref(lat)))
+        _fw.check(_fw.lib().fw_server_release(self._h, ticket))
+        paths, plen = self._out.pop(ticket)
+        return paths, plen, lat.value
+
+    def stats(self) -> dict:
+        s = _fw.ServerStats()
+        _fw.check(_fw.lib().fw_server_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in _fw.ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            _fw.lib().fw_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
         except Exception:
             pass

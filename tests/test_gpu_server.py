@@ -1,0 +1,86 @@
+"""Served form: continuous batching keeps every request's result equal to the
+same request run alone, whatever else is on the GPU, and serves requests
+that arrive while others run."""
+
+import threading
+import time
+
+import numpy as np
+import pytest
+import torch
+
+import fw_inputs as fi
+from gpu_common import cached_graph, check_valid, device_graph
+
+pytestmark = pytest.mark.gpu
+
+ALGOS = ["weighted", "node2vec", "metapath", "ppr"]
+
+
+def _mix(g, n_req, seed0, rng):
+    reqs = []
+    for i in range(n_req):
+        n_q = int(2 ** rng.uniform(0, 11))
+        a = ALGOS[i % 4]
+        L = 100 if a == "ppr" else int(rng.integers(10, 81))
+        reqs.append(dict(algo=a, starts=fi.random_starts(g.n, n_q, seed0 + i), max_len=L, seed=seed0 * 977 + i,
+                         p=2.0, q=0.5, lengths=fi.uniform_lengths(n_q, 0, L, seed0 + 3 * i) if i % 3 == 0 else None))
+    return reqs
+
+
+@pytest.mark.parametrize("mode", ["exact", "fast"])
+def test_alone_equals_in_the_mix(mode):
+    from paper_2404_08364_gb300 import Server
+    g = cached_graph("rmat", 14, 2)
+    dg = device_graph(g)
+    rng = np.random.default_rng(3)
+    reqs = _mix(g, 24, 11, rng)
+    srv = Server(dg, mode=mode, mem_budget=64 << 20)
+    tickets = [srv.submit(**r) for r in reqs]
+    outs = [srv.result(t) for t in tickets]
+    srv.close()
+    for r, (paths, plen, lat) in zip(reqs, outs):
+        alone_p, alone_l = dg.walk(r["algo"], r["starts"].cuda(), r["max_len"], r["seed"], mode=mode, p=2.0, q=0.5,
+                                   lengths=None if r["lengths"] is None else r["lengths"].cuda())
+        assert torch.equal(plen, alone_l.cpu()), r["algo"]
+        assert torch.equal(paths, alone_p.cpu()), r["algo"]
+        assert lat > 0
+
+
+def test_requests_arriving_while_others_run():
+    from paper_2404_08364_gb300 import Server
+    g = cached_graph("rmat", 16, 2)
+    dg = device_graph(g)
+    rng = np.random.default_rng(5)
+    srv = Server(dg, mode="fast", mem_budget=16 << 20, idle_ms=5.0)  # small arena: admission must wait for memory
+    reqs = _mix(g, 60, 101, rng)
+    tickets = []
+    for i, r in enumerate(reqs):
+        tickets.append(srv.submit(**r))
+        if i % 7 == 0:
+            time.sleep(0.002)
+    lat = []
+    for r, t in zip(reqs, tickets):
+        paths, plen, l = srv.result(t)
+        lat.append(l)
+        check_valid(g, paths.cuda(), plen.cuda(), r["algo"])
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs)
+    assert st["arena_used"] == 0
+    assert st["steps"] > 0
+
+
+def test_idle_engine_is_relaunched():
+    from paper_2404_08364_gb300 import Server
+    g = cached_graph("rmat", 12, 2)
+    dg = device_graph(g)
+    srv = Server(dg, mode="exact", mem_budget=8 << 20, idle_ms=2.0)
+    s = fi.random_starts(g.n, 100, 1)
+    a = srv.result(srv.submit("weighted", s, 20, 5))
+    time.sleep(0.1)  # the engine returns after 2 ms of idleness
+    b = srv.result(srv.submit("weighted", s, 20, 5))
+    st = srv.stats()
+    srv.close()
+    assert torch.equal(a[0], b[0])
+    assert st["launches"] >= 2
