@@ -51,10 +51,11 @@ constexpr int SW_MAX = 8;         // walk slots per warp, upper bound
 constexpr int NHUB = 4;           // hub tasks open at once per CTA
 constexpr int NSEG_MAX = 64;      // segments per hub task
 constexpr int NCHUNK_MAX = 64;    // exact warp sampler: chunk sums (d_t <= 8192)
-constexpr int NST = 6;            // TMA ring stages per warp
+constexpr int NST = 3;            // TMA ring stages per warp
 constexpr int CHQ = 32;           // quads per chunk (one per lane)
-constexpr int ST_COL = 0, ST_W = CHQ * 16, ST_ET = CHQ * 32;
-constexpr int STAGE_BYTES = CHQ * 36;  // columns, weights, labels of one chunk
+constexpr int SQ = 2 * CHQ;       // quads per stage: two chunks, lane l holds quads l and l + 32
+constexpr int ST_COL = 0, ST_W = SQ * 16, ST_ET = SQ * 32;
+constexpr int STAGE_BYTES = SQ * 36;  // columns, weights, labels of one stage
 constexpr int ST_EMPTY = 0, ST_READY = 1, ST_HUB = 2, ST_FINISH = 3;
 // hub task control word: state << 24 | next segment to hand out
 constexpr int H_FREE = 0, H_SETUP = 1, H_ACTIVE = 2;
@@ -182,16 +183,16 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
         : "memory");
 }
 
-// A warp's private ring of NST chunk buffers in shared memory, each with its
-// mbarrier and a flag telling whether the chunk came by TMA (0) or must be
-// read from global memory (1: it touches the unpadded end of the arrays).
-// Chunks go through the stages in order; (st, ph) = stage of the next chunk
-// to consume and the barrier phase parity it completes there.
+// A warp's private ring of NST stage buffers in shared memory, each with its
+// mbarrier.  A stage holds SQ quads (256 entries).  Stages go through the
+// ring in order; (st, ph) = stage of the next one to consume and the barrier
+// phase parity it completes there.  A stage that would read past the end of
+// the CSR arrays is not copied (its barrier is just arrived on) and its
+// quads are read from global memory instead: stage_direct() says which.
 struct WarpPipe {
     unsigned char* buf;
     unsigned long long* bar;
-    int* direct;
-    unsigned* mask;  // node2vec membership bits of the current chunk
+    unsigned* mask;  // node2vec membership bits of the current stage (8 words)
     int st;
     uint32_t ph;
 };
@@ -351,23 +352,24 @@ struct BBlock {
     int v[4];
 };
 
-// node2vec membership for a chunk staged in shared memory, driven from B's
-// side: the chunk's valid entries colS[ia, ib) are sorted, so only the B
+// node2vec membership for a stage of N(cur) in shared memory, driven from
+// B's side: the stage's valid entries colS[ia, ib) are sorted, so only the B
 // values inside [colS[ia], colS[ib-1]] can match; each such value (typically
-// a handful per chunk, one per lane) binary-searches the staged chunk and
-// sets its bit in the warp's 128-bit mask.  A chunk whose value range holds
-// more than 256 entries of B (B much denser than this part of N(cur)) is
+// a handful per stage, one per lane) binary-searches the staged entries and
+// sets its bit in the warp's 256-bit mask.  A stage whose value range holds
+// more than 512 entries of B (B much denser than this part of N(cur)) is
 // answered from the entries' side instead, by lockstep binary searches of
-// each lane's four values in B.  Returns this lane's four bits (entries
-// 4 lane .. 4 lane + 3 of the chunk).  Warp-collective.
+// each lane's values in B.  cv[0..3] are this lane's entries at stage
+// positions 4 lane + j, cv[4..7] those at 128 + 4 lane + j; bit i of the
+// result (and of `valid`) belongs to cv[i].  Warp-collective.
 __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B, int pd, BBlock& bb,
-                                                const int* __restrict__ colS, int ia, int ib,
-                                                const int c0, const int c1, const int c2, const int c3,
-                                                unsigned valid, int lane, unsigned* __restrict__ mask) {
+                                                   const int* __restrict__ colS, int ia, int ib,
+                                                   const int (&cv)[8], unsigned valid, int lane,
+                                                   unsigned* __restrict__ mask) {
     if (ia >= ib || pd == 0) return 0u;
     const int amin = colS[ia], amax = colS[ib - 1];
     if (bb.base >= 0) {
-        // common case: the loaded block reaches past this chunk and holds no
+        // common case: the loaded block reaches past this stage and holds no
         // value inside its range: nothing can match, one vote decides it
         const int last = __shfl_sync(FULL, bb.v[3], 31);
         bool in = false;
@@ -375,7 +377,7 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
         for (int i = 0; i < 4; ++i) in |= bb.v[i] >= amin && bb.v[i] <= amax;
         if (last > amax && !__any_sync(FULL, in)) return 0u;
     }
-    if (lane < 4) mask[lane] = 0u;
+    if (lane < 8) mask[lane] = 0u;
     __syncwarp();
     for (int guard = 0; guard < 4; ++guard) {
         if (bb.base < 0) {
@@ -383,45 +385,49 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
             load_b128(B, pd, bb.base, lane, bb.v);
         }
         // (a step normally starts with B's first block already requested by
-        // the caller, overlapping that load with the first chunk's copy)
+        // the caller, overlapping that load with the first stage's copy)
         int last = __shfl_sync(FULL, bb.v[3], 31);
         if (last < amin) {
-            // the whole block lies below this chunk: jump to the chunk's range
+            // the whole block lies below this stage: jump to the stage's range
             bb.base = lower_bound_from(B, pd, bb.base + 128, amin, lane);
             load_b128(B, pd, bb.base, lane, bb.v);
             last = __shfl_sync(FULL, bb.v[3], 31);
         }
         if (bb.base >= pd) break;
         if (last <= amax && guard == 0) {
-            // the chunk's range runs past this block: if B is dense there,
+            // the stage's range runs past this block: if B is dense there,
             // search from the entries' side
             const int ub = lower_bound_from(B, pd, bb.base + 128, amax == INT_BIG - 1 ? INT_BIG : amax + 1, lane);
-            if (ub - bb.base > 256) {
+            if (ub - bb.base > 512) {
                 const int lo = bb.base;
-                int a[4], b[4];
-                const int cv[4] = {c0, c1, c2, c3};
+                unsigned f = 0;
+#pragma unroll 1
+                for (int h = 0; h < 2; ++h) {
+                    int a[4], b[4], x[4];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    a[j] = lo;
-                    b[j] = (valid >> j & 1u) ? ub : lo;
-                }
-                for (;;) {
-                    bool more = false;
+                    for (int j = 0; j < 4; ++j) {
+                        x[j] = h ? cv[4 + j] : cv[j];
+                        a[j] = lo;
+                        b[j] = (valid >> (4 * h + j) & 1u) ? ub : lo;
+                    }
+                    for (;;) {
+                        bool more = false;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if (a[j] < b[j]) {
+                                more = true;
+                                const int mid = (a[j] + b[j]) >> 1;
+                                if (__ldg(B + mid) < x[j]) a[j] = mid + 1;
+                                else b[j] = mid;
+                            }
+                        if (!more) break;
+                    }
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
-                        if (a[j] < b[j]) {
-                            more = true;
-                            const int mid = (a[j] + b[j]) >> 1;
-                            if (__ldg(B + mid) < cv[j]) a[j] = mid + 1;
-                            else b[j] = mid;
-                        }
-                    if (!more) break;
+                        if ((valid >> (4 * h + j) & 1u) && a[j] < ub && __ldg(B + a[j]) == x[j])
+                            f |= 1u << (4 * h + j);
                 }
-                unsigned f = 0;
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if ((valid >> j & 1u) && a[j] < ub && __ldg(B + a[j]) == cv[j]) f |= 1u << j;
-                bb.base = -1;  // the next chunk starts from a fresh search
+                bb.base = -1;  // the next stage starts from a fresh search
                 return f;
             }
         }
@@ -438,14 +444,15 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
                 if (lo < ib && colS[lo] == bv) atomicOr(&mask[lo >> 5], 1u << (lo & 31));
             }
         }
-        if (last > amax) break;  // the block reaches past the chunk: keep it for the next one
+        if (last > amax) break;  // the block reaches past the stage: keep it for the next one
         // every entry of the block is at most amax: move on to the next block
         bb.base += 128;
         if (bb.base >= pd) break;
         load_b128(B, pd, bb.base, lane, bb.v);
     }
     __syncwarp();
-    return (mask[lane >> 3] >> ((lane & 7) * 4)) & 0xFu;
+    const int sh = (lane & 7) * 4;
+    return ((mask[lane >> 3] >> sh) & 0xFu) | (((mask[4 + (lane >> 3)] >> sh) & 0xFu) << 4);
 }
 
 // One lane's four consecutive row entries (an aligned quad of the CSR
@@ -588,34 +595,39 @@ __device__ __noinline__ WarpRes warp_record(WarpRes r, int idx, float w, uint64_
     return r;
 }
 
-// Offer one chunk: lane `lane` holds entries e0 .. e0+3 (row indices) with
-// weights w[0..3]; entries are visited in lane order, then j.
-__device__ __forceinline__ void warp_offer_chunk(WarpRes& R, const float (&w)[4], int e0, int lane, uint64_t seed,
+// Offer one stage: lane `lane` holds the entries of row indices e0 + j
+// (w[j], j < 4) and e0 + 124 + j (w[j], j >= 4), i.e. its quad of each
+// chunk of the stage.  Entries are visited lane by lane, j ascending: any
+// fixed order gives the same law.
+__device__ __forceinline__ void warp_offer_stage(WarpRes& R, const float (&w)[8], int e0, int lane, uint64_t seed,
                                                  uint64_t qid, uint32_t t, uint32_t stream) {
-    const float l0 = w[0], l1 = l0 + w[1], l2 = l1 + w[2], l3 = l2 + w[3];
-    float incl = l3;
+    const float own = ((w[0] + w[1]) + (w[2] + w[3])) + ((w[4] + w[5]) + (w[6] + w[7]));
+    float incl = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const float n = __shfl_up_sync(FULL, incl, o);
         if (lane >= o) incl += n;
     }
     const float tot = __shfl_sync(FULL, incl, 31);
-    if (R.Xh - tot + R.Xl > 0.0f) {  // no record in this chunk (the common case)
+    if (R.Xh - tot + R.Xl > 0.0f) {  // no record in this stage (the common case)
         // X -= tot with the rounding error kept (Fast2Sum: |Xh| > tot here)
         const float sh = R.Xh - tot;
         R.Xl += (R.Xh - sh) - tot;
         R.Xh = sh;
         return;
     }
-    const float excl = incl - l3;
-    const float cum[4] = {excl + l0, excl + l1, excl + l2, excl + l3};
+    // a record falls in this stage: running sums in visiting order
+    float cum[8];
+    cum[0] = (incl - own) + w[0];
+#pragma unroll
+    for (int j = 1; j < 8; ++j) cum[j] = cum[j - 1] + w[j];
     float target = R.Xh + R.Xl;  // a record falls on the first entry whose cumulative weight reaches target
-    int last = -1;               // chunk position (lane * 4 + j) of the last record: each record lies beyond it
+    int last = -1;               // visiting position (lane * 8 + j) of the last record: each record lies beyond it
     for (;;) {
         int jj = -1;
 #pragma unroll
-        for (int j = 3; j >= 0; --j)
-            if (lane * 4 + j > last && w[j] > 0.0f && cum[j] >= target) jj = j;
+        for (int j = 7; j >= 0; --j)
+            if (lane * 8 + j > last && w[j] > 0.0f && cum[j] >= target) jj = j;
         const unsigned m = __ballot_sync(FULL, jj >= 0);
         if (!m) {
             R.Xh = target - tot;
@@ -625,15 +637,16 @@ __device__ __forceinline__ void warp_offer_chunk(WarpRes& R, const float (&w)[4]
         const int L = __ffs(m) - 1;
         float wj = 0.0f, cj = 0.0f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 8; ++j)
             if (j == jj) {
                 wj = w[j];
                 cj = cum[j];
             }
         const float wr = __shfl_sync(FULL, wj, L);
         const float cr = __shfl_sync(FULL, cj, L);
-        const int idx = __shfl_sync(FULL, e0 + jj, L);
-        last = L * 4 + __shfl_sync(FULL, jj, L);
+        const int jl = __shfl_sync(FULL, jj, L);
+        const int idx = __shfl_sync(FULL, e0, L) + jl + (jl >= 4 ? 124 : 0);
+        last = L * 8 + jl;
         R = warp_record(R, idx, wr, seed, qid, t, stream);
         target = cr + R.Xh;
     }
@@ -650,57 +663,52 @@ __device__ __forceinline__ int pick_in_quad(const uint32_t (&w)[4], unsigned lon
     return 3;
 }
 
-// Lane 0: start loading quads [qs, qs + nq) (qs a multiple of 4) into stage
-// st of the warp's ring.
+// Whether a stage of nq quads from qs is read from global memory instead of
+// being copied (it would run past the end of the CSR arrays).  Uniform.
+__device__ __forceinline__ bool stage_direct(const GraphDev& g, long long qs, int nq) {
+    return 4 * (qs + ((nq + 3) & ~3)) > g.m;
+}
+
+// Lane 0: start loading quads [qs, qs + nq) (qs a multiple of 4, nq <= SQ)
+// into stage st of the warp's ring.
 template <int MODE>
 __device__ __forceinline__ void pipe_issue(const GraphDev& g, WarpPipe& P, int st, long long qs, int nq,
                                            bool labels) {
     unsigned char* b = P.buf + st * STAGE_BYTES;
-    const long long nq4 = (nq + 3) & ~3;
-    if (4 * (qs + nq4) <= g.m) {
-        P.direct[st] = 0;
-        const uint32_t bytes = (uint32_t)(nq4 * 32 + (labels ? nq4 * 4 : 0));
-        mbar_arrive_expect_tx(&P.bar[st], bytes);
-        tma_load_1d(b + ST_COL, g.col + 4 * qs, (uint32_t)(nq4 * 16), &P.bar[st]);
-        if (MODE == MODE_EXACT) tma_load_1d(b + ST_W, g.w_u32 + 4 * qs, (uint32_t)(nq4 * 16), &P.bar[st]);
-        else tma_load_1d(b + ST_W, g.w_f32 + 4 * qs, (uint32_t)(nq4 * 16), &P.bar[st]);
-        if (labels) tma_load_1d(b + ST_ET, g.etype + 4 * qs, (uint32_t)(nq4 * 4), &P.bar[st]);
+    if (!stage_direct(g, qs, nq)) {
+        const uint32_t nq4 = (uint32_t)((nq + 3) & ~3);
+        mbar_arrive_expect_tx(&P.bar[st], nq4 * 32 + (labels ? nq4 * 4 : 0));
+        tma_load_1d(b + ST_COL, g.col + 4 * qs, nq4 * 16, &P.bar[st]);
+        if (MODE == MODE_EXACT) tma_load_1d(b + ST_W, g.w_u32 + 4 * qs, nq4 * 16, &P.bar[st]);
+        else tma_load_1d(b + ST_W, g.w_f32 + 4 * qs, nq4 * 16, &P.bar[st]);
+        if (labels) tma_load_1d(b + ST_ET, g.etype + 4 * qs, nq4 * 4, &P.bar[st]);
     } else {
-        P.direct[st] = 1;
         mbar_arrive(&P.bar[st]);
     }
 }
 
-// Quad `lane` of a landed chunk (quads [qs, qs + 32)), masked to quads below
-// qb and entries inside the row [c.beg, end), MetaPath label applied.
+// This lane's quad of chunk h (0 or 1) of a landed stage whose entry 0 is
+// row index r0; entries at row indices outside [0, lim) are masked out,
+// MetaPath labels applied.
 template <int MODE>
-__device__ __forceinline__ void stage_quad(const GraphDev& g, const StepCtx& c, const WarpPipe& P, int st,
-                                           long long qs, long long qb, long long end, int lane, Quad<MODE>& Q) {
-    const long long q = qs + lane;
-    if (q >= qb) {
-        clear_quad(Q);
-        return;
-    }
-    if (P.direct[st]) {
-        load_quad<MODE>(g, c, q, end, Q);
-        return;
-    }
-    const unsigned char* b = P.buf + st * STAGE_BYTES;
-    const int4 cv = *reinterpret_cast<const int4*>(b + ST_COL + lane * 16);
+__device__ __forceinline__ void stage_quad(const StepCtx& c, const unsigned char* b, int h, int r0, int lim, int lane,
+                                           Quad<MODE>& Q) {
+    const int o = h * (CHQ * 16) + lane * 16;
+    const int4 cv = *reinterpret_cast<const int4*>(b + ST_COL + o);
     Q.c[0] = cv.x; Q.c[1] = cv.y; Q.c[2] = cv.z; Q.c[3] = cv.w;
     if (MODE == MODE_EXACT) {
-        const uint4 wv = *reinterpret_cast<const uint4*>(b + ST_W + lane * 16);
+        const uint4 wv = *reinterpret_cast<const uint4*>(b + ST_W + o);
         Q.w[0] = wv.x; Q.w[1] = wv.y; Q.w[2] = wv.z; Q.w[3] = wv.w;
     } else {
-        const float4 wv = *reinterpret_cast<const float4*>(b + ST_W + lane * 16);
+        const float4 wv = *reinterpret_cast<const float4*>(b + ST_W + o);
         Q.w[0] = wv.x; Q.w[1] = wv.y; Q.w[2] = wv.z; Q.w[3] = wv.w;
     }
-    const int et = c.algo == FW_METAPATH ? *reinterpret_cast<const int*>(b + ST_ET + lane * 4) : 0;
+    const int et = c.algo == FW_METAPATH ? *reinterpret_cast<const int*>(b + ST_ET + h * (CHQ * 4) + lane * 4) : 0;
     Q.valid = 0;
-    const int rel = (int)((q << 2) - c.beg);  // row index of entry 0 of the quad
+    const int rel = r0 + h * (4 * CHQ) + 4 * lane;  // row index of entry 0 of the quad
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        if ((unsigned)(rel + j) < (unsigned)c.d) {
+        if ((unsigned)(rel + j) < (unsigned)lim) {
             Q.valid |= 1u << j;
             if (c.algo == FW_METAPATH && (int)(int8_t)(et >> (8 * j)) != c.want) Q.w[j] = 0;
         } else {
@@ -711,24 +719,29 @@ __device__ __forceinline__ void stage_quad(const GraphDev& g, const StepCtx& c, 
 }
 
 // Stream quads [qa, qb) (qa a multiple of 4) of the row [c.beg, end) through
-// the warp's TMA ring, NST - 1 chunks ahead: weights with the node2vec
+// the warp's TMA ring, NST - 1 stages ahead: weights with the node2vec
 // factors applied, then (fast) the warp's reservoir drawing from random
 // stream rng_stream, or (exact) each lane's running sum and, if chunk_sums
-// is given, one warp total per chunk.  False if a copy never landed.
+// is given, one warp total per 128-entry chunk.  False if a copy never
+// landed.
 template <int MODE>
 __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, long long qa, long long qb,
                                            long long end, int lane, int* __restrict__ win, WarpPipe& P,
                                            WarpRes& res, unsigned long long& lane_sum,
                                            unsigned long long* __restrict__ chunk_sums, uint32_t rng_stream,
                                            uint64_t seed, uint64_t qid, uint32_t t) {
-    const int nch = (int)((qb - qa + CHQ - 1) / CHQ);
+    const int nst = (int)((qb - qa + SQ - 1) / SQ);
     const bool labels = c.algo == FW_METAPATH;
+    // row indices: of the range's first staged entry, and the end of the
+    // range (entries at or past it are masked out)
+    const int r_a = (int)((qa << 2) - c.beg);
+    const int lim = (int)min((long long)c.d, (qb << 2) - c.beg);
     if (lane == 0) {
         int ist = P.st;
         uint32_t iph = P.ph;
-        for (int k = 0; k < nch && k < NST; ++k) {
-            pipe_issue<MODE>(g, P, ist, qa + (long long)k * CHQ, (int)min((long long)CHQ, qb - qa - (long long)k * CHQ),
-                             labels);
+        for (int k = 0; k < nst && k < NST; ++k) {
+            const long long qs = qa + (long long)k * SQ;
+            pipe_issue<MODE>(g, P, ist, qs, (int)min((long long)SQ, qb - qs), labels);
             ring_next(ist, iph);
         }
     }
@@ -738,58 +751,71 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
     const bool n2v = c.algo == FW_NODE2VEC && c.prev >= 0;
     if (n2v && qa == ((c.beg >> 2) & ~3ll)) {
         // a whole row (or its first segment): start loading N(prev)'s first
-        // block now, while the first chunk is still on its way
+        // block now, while the first stage is still on its way
         bb.base = 0;
         load_b128(g.col + c.pbeg, c.pdeg, 0, lane, bb.v);
     }
     bool ok = true;
-    for (int k = 0; k < nch; ++k) {
+    for (int k = 0; k < nst; ++k) {
         const int st = P.st;
-        const long long qs = qa + (long long)k * CHQ;
+        const long long qs = qa + (long long)k * SQ;
+        const int nq = (int)min((long long)SQ, qb - qs);
+        const int r0 = r_a + k * (4 * SQ);
         if (!mbar_wait_bounded(&P.bar[st], P.ph)) ok = false;
         if (!__all_sync(FULL, ok)) {
             // let the copies already issued land before giving up
             if (lane == 0) {
                 int dst = st;
                 uint32_t dph = P.ph;
-                for (int kk = k + 1; kk < nch && kk < k + NST; ++kk) {
+                for (int kk = k + 1; kk < nst && kk < k + NST; ++kk) {
                     ring_next(dst, dph);
                     mbar_wait_bounded(&P.bar[dst], dph);
                 }
             }
             return false;
         }
-        Quad<MODE> cur;
-        stage_quad<MODE>(g, c, P, st, qs, qb, end, lane, cur);
-        if (n2v) {
-            if (P.direct[st]) {
-                n2v_apply<MODE>(g, c, cur, pos, lane, win);
-            } else {
-                // entries [ia, ib) of the staged chunk belong to this row range
-                const long long e0 = qs << 2;
-                const int ia = (int)max(0ll, c.beg - e0);
-                const int ib = (int)min(min((long long)CHQ * 4, end - e0), (qb - qs) << 2);
-                const int* colS = reinterpret_cast<const int*>(P.buf + st * STAGE_BYTES + ST_COL);
-                const unsigned mem = members_staged(g.col + c.pbeg, c.pdeg, bb, colS, ia, ib, cur.c[0], cur.c[1],
-                                                    cur.c[2], cur.c[3], cur.valid, lane, P.mask);
-                n2v_factors<MODE>(c, cur, mem);
+        Quad<MODE> h0, h1;
+        if (stage_direct(g, qs, nq)) {
+            // the end of the arrays: plain loads, the entries' side membership
+            if (lane < nq) load_quad<MODE>(g, c, qs + lane, end, h0);
+            else clear_quad(h0);
+            if (lane + CHQ < nq) load_quad<MODE>(g, c, qs + CHQ + lane, end, h1);
+            else clear_quad(h1);
+            n2v_apply<MODE>(g, c, h0, pos, lane, win);
+            n2v_apply<MODE>(g, c, h1, pos, lane, win);
+        } else {
+            const unsigned char* b = P.buf + st * STAGE_BYTES;
+            stage_quad<MODE>(c, b, 0, r0, lim, lane, h0);
+            stage_quad<MODE>(c, b, 1, r0, lim, lane, h1);
+            if (n2v) {
+                // staged entries [ia, ib) belong to this range of the row
+                const int ia = max(0, -r0);
+                const int ib = min(4 * SQ, lim - r0);
+                const int cv[8] = {h0.c[0], h0.c[1], h0.c[2], h0.c[3], h1.c[0], h1.c[1], h1.c[2], h1.c[3]};
+                const unsigned mem = members_staged(g.col + c.pbeg, c.pdeg, bb, reinterpret_cast<const int*>(b + ST_COL),
+                                                    ia, ib, cv, h0.valid | (h1.valid << 4), lane, P.mask);
+                n2v_factors<MODE>(c, h0, mem & 0xFu);
+                n2v_factors<MODE>(c, h1, mem >> 4);
             }
         }
         __syncwarp();  // every lane is done with the stage: it may be refilled
-        if (lane == 0 && k + NST < nch) {
-            const long long qn = qa + (long long)(k + NST) * CHQ;
-            pipe_issue<MODE>(g, P, st, qn, (int)min((long long)CHQ, qb - qn), labels);
+        if (lane == 0 && k + NST < nst) {
+            const long long qn = qa + (long long)(k + NST) * SQ;
+            pipe_issue<MODE>(g, P, st, qn, (int)min((long long)SQ, qb - qn), labels);
         }
         ring_next(P.st, P.ph);
         if (MODE == MODE_FAST) {
-            const float wf[4] = {(float)cur.w[0], (float)cur.w[1], (float)cur.w[2], (float)cur.w[3]};
-            warp_offer_chunk(res, wf, (int)(((qs + lane) << 2) - c.beg), lane, seed, qid, t, rng_stream);
+            const float wf[8] = {(float)h0.w[0], (float)h0.w[1], (float)h0.w[2], (float)h0.w[3],
+                                 (float)h1.w[0], (float)h1.w[1], (float)h1.w[2], (float)h1.w[3]};
+            warp_offer_stage(res, wf, r0 + 4 * lane, lane, seed, qid, t, rng_stream);
         } else {
-            const unsigned long long s4 = (unsigned long long)cur.w[0] + cur.w[1] + cur.w[2] + cur.w[3];
-            lane_sum += s4;
+            const unsigned long long s0 = (unsigned long long)h0.w[0] + h0.w[1] + h0.w[2] + h0.w[3];
+            const unsigned long long s1 = (unsigned long long)h1.w[0] + h1.w[1] + h1.w[2] + h1.w[3];
+            lane_sum += s0 + s1;
             if (chunk_sums) {
-                const unsigned long long cs = warp_sum_u64(s4);
-                if (lane == 0 && k < NCHUNK_MAX) chunk_sums[k] = cs;
+                const unsigned long long cs0 = warp_sum_u64(s0), cs1 = warp_sum_u64(s1);
+                if (lane == 0 && 2 * k < NCHUNK_MAX) chunk_sums[2 * k] = cs0;
+                if (lane == 0 && 2 * k + 1 < NCHUNK_MAX) chunk_sums[2 * k + 1] = cs1;
             }
         }
     }
@@ -1025,15 +1051,14 @@ __device__ __forceinline__ void hub_merge(const GraphDev& g, const ReqDev* __res
 }
 
 // Per-warp dynamic shared memory: the TMA ring, the node2vec window, (exact
-// mode) the chunk sums, the ring's barriers and direct flags.
+// mode) the chunk sums, the ring's barriers and the membership mask.
 template <int MODE>
 struct WarpSmem {
     static constexpr int WIN_OFF = NST * STAGE_BYTES;
     static constexpr int SUMS_OFF = WIN_OFF + WIN * 4;
     static constexpr int BAR_OFF = SUMS_OFF + (MODE == MODE_EXACT ? NCHUNK_MAX * 8 : 0);
-    static constexpr int DIRECT_OFF = BAR_OFF + NST * 8;
-    static constexpr int MASK_OFF = DIRECT_OFF + NST * 4;
-    static constexpr int BYTES = (MASK_OFF + 16 + 127) & ~127;
+    static constexpr int MASK_OFF = BAR_OFF + NST * 8;
+    static constexpr int BYTES = (MASK_OFF + 32 + 127) & ~127;
 };
 
 // ------------------------------------------------------------- the engine
@@ -1041,7 +1066,7 @@ struct WarpSmem {
 // Resident CTAs per SM the register budget is cut for: 24 warps per SM at
 // 256 threads (the engine is latency-bound; occupancy pays more than the
 // few registers it costs).
-constexpr int min_ctas(int nt) { return nt >= 512 ? 1 : (nt >= 256 ? 3 : 6); }
+constexpr int min_ctas(int nt) { return nt >= 512 ? 1 : (nt >= 256 ? 3 : 5); }
 
 template <int MODE, int NT>
 __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, const __grid_constant__ ReqTable tab, int n_req,
@@ -1060,7 +1085,6 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
     WarpPipe P;
     P.buf = mine;
     P.bar = reinterpret_cast<unsigned long long*>(mine + WarpSmem<MODE>::BAR_OFF);
-    P.direct = reinterpret_cast<int*>(mine + WarpSmem<MODE>::DIRECT_OFF);
     P.mask = reinterpret_cast<unsigned*>(mine + WarpSmem<MODE>::MASK_OFF);
     P.st = 0;
     P.ph = 0;
@@ -1078,6 +1102,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
     bool exhausted = false;
     int rr = 0;
     unsigned long long idle_since = 0;
+    unsigned nap = 128;  // idle back-off (ns)
 
     for (;;) {
         // ------------------------------------------------ choose the work
@@ -1087,8 +1112,6 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
         long long qa, qb;
         uint64_t seed, qid;
         uint32_t t, stream;
-        int nunits = 1;          // segments this warp samples in a row (1, or a hub
-        long long unit_q = 0;    // task's segments when no task entry was free)
         unsigned long long* sums = nullptr;
         int h, j;
         int s = -1;
@@ -1234,7 +1257,10 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                     break;
                 }
                 if (__shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.abort_flag : 0, 0)) break;
-                __nanosleep(200);
+                // back off while nothing turns up: an idle warp's polling
+                // takes issue slots from the warps that are scanning
+                __nanosleep(nap);
+                nap = min(nap * 2u, 1024u);
                 continue;
             }
 
@@ -1297,43 +1323,27 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                     }
                 }
                 hh = __shfl_sync(FULL, hh, 0);
-                if (hh >= 0) continue;   // the walk waits for the CTA sampler; go on with other work
-                if (too_long) continue;  // no free entry: retry after helping the open ones
-                if (MODE == MODE_FAST) {
-                    // no free entry: this warp samples the hub task's segments
-                    // itself, with the same random streams, so the result does
-                    // not depend on who did the work
-                    const long long nq = qb - qa;
-                    long long sq = max((long long)seg_q, (nq + NSEG_MAX - 1) / NSEG_MAX);
-                    unit_q = (sq + 31) & ~31ll;
-                    nunits = (int)((nq + unit_q - 1) / unit_q);
-                }
+                if (hh >= 0) continue;  // the walk waits for the CTA sampler; go on with other work
+                // no free task entry: the walk stays ready and is published
+                // on a later visit, after this warp has helped the open tasks
+                // (so a hub row is always sampled segment by segment with the
+                // task's random streams, whoever finds the entry free)
+                __nanosleep(nap);
+                nap = min(nap * 2u, 1024u);
+                continue;
             }
             stream = 0;
             if (MODE == MODE_EXACT) sums = chunk_sums;
         }
         idle_since = 0;
+        nap = 128;
 
         // ------------------------------------ stream the row range (one site)
         WarpRes res;
+        res.init();
         unsigned long long lane_sum = 0;
         const long long end = c.beg + c.d;
-        if (nunits == 1) unit_q = qb - qa;
-        float best_tau = __int_as_float(0x7f800000);
-        int best_sel = -1;
-        bool ok = true;
-        for (int u = 0; u < nunits && ok; ++u) {
-            const long long ua = qa + (long long)u * unit_q, ub = min(qb, ua + unit_q);
-            res.init();
-            ok = scan_range<MODE>(g, c, ua, ub, end, lane, win, P, res, lane_sum, sums,
-                                  nunits > 1 ? (uint32_t)u : stream, seed, qid, t);
-            // merge segments like the hub task does: smaller race time, then smaller index
-            if (res.sel >= 0 && (best_sel < 0 || res.tau < best_tau || (res.tau == best_tau && res.sel < best_sel))) {
-                best_tau = res.tau;
-                best_sel = res.sel;
-            }
-        }
-        if (!ok) {
+        if (!scan_range<MODE>(g, c, qa, qb, end, lane, win, P, res, lane_sum, sums, stream, seed, qid, t)) {
             if (lane == 0) atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
             break;
         }
@@ -1346,7 +1356,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
         int sel = -1;
         uint32_t oz = 0xFFFFFFFFu;
         if (MODE == MODE_FAST) {
-            sel = best_sel;
+            sel = res.sel;
             if (sel >= 0 && R->algo == FW_PPR) oz = step_block(seed, qid, t).z;
         } else {
             const unsigned long long W = warp_sum_u64(lane_sum);
@@ -1368,7 +1378,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
             if (sel < 0) {
                 sm.state[s] = ST_FINISH;  // nothing selectable: the walk stops here
             } else {
-                cnt.step(c.d, c.algo, nunits > 1);
+                cnt.step(c.d, c.algo, false);
                 commit(g, sm, *R, s, c, __ldg(g.col + c.beg + sel), oz);
             }
         }
@@ -1430,7 +1440,7 @@ cudaError_t launch_serve_one(const GraphDev& g, const ServeDev& sv, Scratch* scr
 
 }  // namespace
 
-Tuning default_tuning() { return Tuning{256, 16, 16384, 0}; }
+Tuning default_tuning() { return Tuning{128, 16, 16384, 0}; }
 
 Tuning sanitize_tuning(Tuning t) {
     const Tuning d = default_tuning();
