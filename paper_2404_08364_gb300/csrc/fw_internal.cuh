@@ -121,20 +121,28 @@ struct ReqTable {
 };
 
 // Served form: requests live in a device ring that the host keeps extending
-// while the kernel runs; the kernel claims published queries, and the last
-// walk of a request stamps its completion word in host memory.  All waits on
-// the host words are bounded by idle_ns.
+// (by stream-ordered copies) while the kernel runs; the kernel claims
+// published queries, and the last walk of a request stamps its completion
+// word in host memory.  The host ends a launch by setting `stop` once it has
+// been idle for a while: warps then claim nothing new, finish the walks they
+// hold and return.
 struct ServeDev {
     ReqDev* ring;                                 // device, maxr entries (null: batch launch)
     int maxr;
     unsigned long long* done;                     // device, per ring slot: walks retired
-    unsigned long long* cursor;                   // device: next query to hand out
-    const volatile unsigned long long* pub_q;     // mapped host: queries published so far
-    const volatile unsigned long long* pub_r;     // mapped host: requests published so far
-    const volatile int* stop;                     // mapped host: drain and return
+    // device, per ring slot: the query hand-out counter.  Admission sets it
+    // to kTakenBase - n_q; a warp claims query k of the slot's request when
+    // atomicAdd returns kTakenBase - n_q + k < kTakenBase.  The counter alone
+    // decides whether a claim is valid, so a warp holding a stale ring id
+    // can never claim from a slot that is being refilled.
+    unsigned long long* taken;
+    unsigned long long* head;                     // device: oldest ring id that may still hand out queries
+    const volatile long long* pub_r;              // device: requests published (written by host copies)
+    const volatile int* stop;                     // device: drain and return (written by a host copy)
     volatile unsigned long long* complete;        // mapped host: per ring slot, nonzero when done
-    unsigned long long idle_ns;                   // return after this long without any work
 };
+
+constexpr unsigned long long kTakenBase = 1ull << 62;
 
 struct Tuning {
     int block_threads;

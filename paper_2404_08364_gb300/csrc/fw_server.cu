@@ -6,8 +6,10 @@
 // a request that arrives while others are on the GPU starts as soon as warps
 // free up, and shares the device with them.  The last walk of a request
 // stamps a completion word in pinned host memory; a host thread copies the
-// results out, frees the arena space and admits waiting requests.  The engine
-// returns after an idle period and is relaunched when work arrives.
+// results out, frees the arena space and admits waiting requests.  After an
+// idle period the host sets the engine's stop word: warps claim nothing new,
+// finish the walks they hold and return together, and the engine is
+// relaunched when work arrives.
 //
 // A request's walks use request-local query ids and the request's own seed,
 // so its paths are the same alone and in any mix (bit for bit in exact mode;
@@ -115,18 +117,30 @@ struct fw_server {
     // device
     ReqDev* ring = nullptr;
     unsigned long long* done = nullptr;
-    unsigned long long* cursor = nullptr;
+    unsigned long long* taken = nullptr;   // per ring slot: query hand-out counter
+    unsigned long long* head = nullptr;    // oldest ring id that may still hand out queries
+    long long* pub_r = nullptr;            // requests published
+    int* stop = nullptr;
     Scratch* scratch = nullptr;
     unsigned char* arena_mem = nullptr;
+    // pinned host staging, one entry per ring slot: the sources of the
+    // stream-ordered copies that publish a request (a slot's entry is not
+    // rewritten before its request completes, long after its copies ran)
+    ReqDev* h_ring = nullptr;
+    unsigned long long* h_taken = nullptr;
+    long long* h_pub_r = nullptr;
+    int* h_stop = nullptr;                 // {0, 1}: the values copied into `stop`
+    unsigned long long* h_zero = nullptr;  // 0: copied into a slot's retire count
     // pinned, mapped host words
-    unsigned long long* h_pub = nullptr;   // [0] queries, [1] requests
-    int* h_stop = nullptr;
     unsigned long long* h_complete = nullptr;  // maxr
     ServeDev sv;
     Arena arena;
     cudaStream_t kstream = nullptr, cstream = nullptr;
     cudaEvent_t kdone = nullptr;
     bool kernel_running = false;
+    bool stop_sent = false;               // this launch has been asked to return
+    Clock::duration idle;                 // host idle time before the engine is stopped
+    Clock::time_point last_busy;
     uint64_t launches = 0;
     // requests
     std::mutex mu;
@@ -136,7 +150,6 @@ struct fw_server {
     std::vector<Ticket*> ring_owner;   // ticket holding each ring slot
     uint64_t next_ticket = 1;
     int64_t next_ring = 0;
-    unsigned long long published_q = 0;
     bool shutdown = false;
     int error = 0;
     std::thread worker;
@@ -207,28 +220,35 @@ void worker_loop(fw_server* S) {
                 S->cv.notify_all();
                 continue;
             }
+            // stream-ordered publication: inputs, the ring entry, the
+            // retire count, the hand-out counter (from here on the engine
+            // may claim the request's queries), then the published count
+            S->h_complete[slot] = 0;
             stage_request(S, T, &rd);
             rd.n_q = T->req.n_q;
-            rd.q_begin = (int64_t)S->published_q;
+            rd.q_begin = 0;
             rd.q_id0 = T->req.q_id0;
-            cudaMemcpyAsync(&S->ring[slot], &rd, sizeof rd, cudaMemcpyHostToDevice, S->cstream);
-            cudaMemsetAsync(&S->done[slot], 0, sizeof(unsigned long long), S->cstream);
-            cudaError_t e = cudaStreamSynchronize(S->cstream);
+            S->h_ring[slot] = rd;
+            S->h_taken[slot] = kTakenBase - (unsigned long long)T->req.n_q;
+            S->h_pub_r[slot] = S->next_ring + 1;
+            cudaMemcpyAsync(&S->ring[slot], &S->h_ring[slot], sizeof(ReqDev), cudaMemcpyHostToDevice, S->cstream);
+            // (a copy, not a memset: a memset runs as a kernel, and the
+            // resident engine may hold every SM until these words land)
+            cudaMemcpyAsync(&S->done[slot], S->h_zero, sizeof(unsigned long long), cudaMemcpyHostToDevice, S->cstream);
+            cudaMemcpyAsync(&S->taken[slot], &S->h_taken[slot], sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                            S->cstream);
+            cudaError_t e = cudaMemcpyAsync(S->pub_r, &S->h_pub_r[slot], sizeof(long long), cudaMemcpyHostToDevice,
+                                            S->cstream);
             if (e != cudaSuccess) {
                 S->error = FW_ECUDA;
                 S->shutdown = true;
                 break;
             }
-            S->h_complete[slot] = 0;
             S->ring_owner[slot] = T;
             T->ring_id = S->next_ring++;
             T->state = T_RUNNING;
             T->t_admit = Clock::now();
             S->pending.pop_front();
-            // publish: the request first, then its queries
-            __atomic_store_n(&S->h_pub[1], (unsigned long long)S->next_ring, __ATOMIC_RELEASE);
-            S->published_q += (unsigned long long)T->req.n_q;
-            __atomic_store_n(&S->h_pub[0], S->published_q, __ATOMIC_RELEASE);
             busy = true;
         }
         // ---- keep the engine running while admitted work is unfinished ----
@@ -237,7 +257,9 @@ void worker_loop(fw_server* S) {
             if (S->ring_owner[i] && S->ring_owner[i]->state == T_RUNNING) unfinished = true;
         if (S->kernel_running && cudaEventQuery(S->kdone) == cudaSuccess) S->kernel_running = false;
         if (unfinished && !S->kernel_running && !S->shutdown) {
-            cudaError_t e = launch_serve(S->g, S->mode, S->sv, S->scratch, S->tuning, S->kstream);
+            // clear the stop word behind the previous launch, then launch
+            cudaError_t e = cudaMemcpyAsync(S->stop, &S->h_stop[0], sizeof(int), cudaMemcpyHostToDevice, S->kstream);
+            if (e == cudaSuccess) e = launch_serve(S->g, S->mode, S->sv, S->scratch, S->tuning, S->kstream);
             if (e == cudaSuccess) e = cudaEventRecord(S->kdone, S->kstream);
             if (e != cudaSuccess) {
                 S->error = FW_ECUDA;
@@ -245,7 +267,15 @@ void worker_loop(fw_server* S) {
                 break;
             }
             S->kernel_running = true;
+            S->stop_sent = false;
             ++S->launches;
+        }
+        // ---- idle for a while: let the engine return (it drains first) ----
+        const Clock::time_point now = Clock::now();
+        if (unfinished || !S->pending.empty()) S->last_busy = now;
+        if (S->kernel_running && !S->stop_sent && !unfinished && S->pending.empty() && now - S->last_busy > S->idle) {
+            cudaMemcpyAsync(S->stop, &S->h_stop[1], sizeof(int), cudaMemcpyHostToDevice, S->cstream);
+            S->stop_sent = true;
         }
         // ---- completions: copy results out, then release the space ----
         for (int i = 0; i < S->maxr; ++i) {
@@ -307,17 +337,28 @@ extern "C" int fw_server_create(fw_graph* graph, int32_t mode, uint64_t mem_budg
     };
     chk(cudaMalloc(&S->ring, sizeof(ReqDev) * (size_t)S->maxr));
     chk(cudaMalloc(&S->done, sizeof(unsigned long long) * (size_t)S->maxr));
-    chk(cudaMalloc(&S->cursor, sizeof(unsigned long long)));
+    chk(cudaMalloc(&S->taken, sizeof(unsigned long long) * (size_t)S->maxr));
+    chk(cudaMalloc(&S->head, sizeof(unsigned long long)));
+    chk(cudaMalloc(&S->pub_r, sizeof(long long)));
+    chk(cudaMalloc(&S->stop, sizeof(int)));
     chk(cudaMalloc(&S->scratch, sizeof(Scratch)));
     chk(cudaMalloc(&S->arena_mem, (size_t)mem_budget));
-    chk(cudaHostAlloc(&S->h_pub, 2 * sizeof(unsigned long long), cudaHostAllocMapped));
-    chk(cudaHostAlloc(&S->h_stop, sizeof(int), cudaHostAllocMapped));
+    chk(cudaHostAlloc(&S->h_ring, sizeof(ReqDev) * (size_t)S->maxr, cudaHostAllocDefault));
+    chk(cudaHostAlloc(&S->h_taken, sizeof(unsigned long long) * (size_t)S->maxr, cudaHostAllocDefault));
+    chk(cudaHostAlloc(&S->h_pub_r, sizeof(long long) * (size_t)S->maxr, cudaHostAllocDefault));
+    chk(cudaHostAlloc(&S->h_stop, 2 * sizeof(int), cudaHostAllocDefault));
+    chk(cudaHostAlloc(&S->h_zero, sizeof(unsigned long long), cudaHostAllocDefault));
     chk(cudaHostAlloc(&S->h_complete, sizeof(unsigned long long) * (size_t)S->maxr, cudaHostAllocMapped));
     chk(cudaStreamCreateWithFlags(&S->kstream, cudaStreamNonBlocking));
     chk(cudaStreamCreateWithFlags(&S->cstream, cudaStreamNonBlocking));
     chk(cudaEventCreateWithFlags(&S->kdone, cudaEventDisableTiming));
     if (e == cudaSuccess) {
-        chk(cudaMemset(S->cursor, 0, sizeof(unsigned long long)));
+        // every slot starts exhausted: nothing can be claimed before admission
+        for (int i = 0; i < S->maxr; ++i) S->h_taken[i] = kTakenBase;
+        chk(cudaMemcpy(S->taken, S->h_taken, sizeof(unsigned long long) * (size_t)S->maxr, cudaMemcpyHostToDevice));
+        chk(cudaMemset(S->head, 0, sizeof(unsigned long long)));
+        chk(cudaMemset(S->pub_r, 0, sizeof(long long)));
+        chk(cudaMemset(S->stop, 0, sizeof(int)));
         chk(cudaMemset(S->scratch, 0, sizeof(Scratch)));
         chk(cudaMemset(S->done, 0, sizeof(unsigned long long) * (size_t)S->maxr));
     }
@@ -327,24 +368,24 @@ extern "C" int fw_server_create(fw_graph* graph, int32_t mode, uint64_t mem_budg
         return fail_s(e == cudaErrorMemoryAllocation ? FW_ENOMEM : FW_ECUDA, "fw_server_create: %s",
                       cudaGetErrorString(e));
     }
-    S->h_pub[0] = S->h_pub[1] = 0;
-    *S->h_stop = 0;
+    S->h_stop[0] = 0;
+    S->h_stop[1] = 1;
+    *S->h_zero = 0;
     memset(S->h_complete, 0, sizeof(unsigned long long) * (size_t)S->maxr);
     ServeDev& sv = S->sv;
     sv.ring = S->ring;
     sv.maxr = S->maxr;
     sv.done = S->done;
-    sv.cursor = S->cursor;
-    unsigned long long *dpub = nullptr, *dcomp = nullptr;
-    int* dstop = nullptr;
-    cudaHostGetDevicePointer((void**)&dpub, S->h_pub, 0);
-    cudaHostGetDevicePointer((void**)&dstop, S->h_stop, 0);
+    sv.taken = S->taken;
+    sv.head = S->head;
+    sv.pub_r = S->pub_r;
+    sv.stop = S->stop;
+    unsigned long long* dcomp = nullptr;
     cudaHostGetDevicePointer((void**)&dcomp, S->h_complete, 0);
-    sv.pub_q = dpub;
-    sv.pub_r = dpub + 1;
-    sv.stop = dstop;
     sv.complete = dcomp;
-    sv.idle_ns = (unsigned long long)((idle_ms > 0 ? idle_ms : 20.0) * 1e6);
+    S->idle = std::chrono::duration_cast<Clock::duration>(
+        std::chrono::duration<double, std::milli>(idle_ms > 0 ? idle_ms : 20.0));
+    S->last_busy = Clock::now();
     S->arena.reset((size_t)mem_budget);
     S->ring_owner.assign(S->maxr, nullptr);
     S->worker = std::thread(worker_loop, S);
@@ -462,7 +503,9 @@ extern "C" void fw_server_destroy(fw_server* S) {
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(S->device);
-    if (S->h_stop) *S->h_stop = 1;  // a running engine drains and returns
+    // a running engine drains and returns
+    if (S->stop && S->h_stop && S->cstream)
+        cudaMemcpyAsync(S->stop, &S->h_stop[1], sizeof(int), cudaMemcpyHostToDevice, S->cstream);
     if (S->kstream) cudaStreamSynchronize(S->kstream);
     if (S->cstream) cudaStreamSynchronize(S->cstream);
     for (auto& kv : S->tickets) {
@@ -471,11 +514,17 @@ extern "C" void fw_server_destroy(fw_server* S) {
     }
     cudaFree(S->ring);
     cudaFree(S->done);
-    cudaFree(S->cursor);
+    cudaFree(S->taken);
+    cudaFree(S->head);
+    cudaFree(S->pub_r);
+    cudaFree(S->stop);
     cudaFree(S->scratch);
     cudaFree(S->arena_mem);
-    if (S->h_pub) cudaFreeHost(S->h_pub);
+    if (S->h_ring) cudaFreeHost(S->h_ring);
+    if (S->h_taken) cudaFreeHost(S->h_taken);
+    if (S->h_pub_r) cudaFreeHost(S->h_pub_r);
     if (S->h_stop) cudaFreeHost(S->h_stop);
+    if (S->h_zero) cudaFreeHost(S->h_zero);
     if (S->h_complete) cudaFreeHost(S->h_complete);
     if (S->kdone) cudaEventDestroy(S->kdone);
     if (S->kstream) cudaStreamDestroy(S->kstream);

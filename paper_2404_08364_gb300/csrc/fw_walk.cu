@@ -87,13 +87,13 @@ struct HubTask {
     uint64_t seed;
     uint64_t qid;
     uint32_t t;
-    int req;
     unsigned long long seg_sum[NSEG_MAX];  // exact
 };
 
 template <int NT>
 struct __align__(16) Smem {
     static constexpr int NS = (NT / 32) * SW_MAX;
+    ReqDev rq[NS];        // each walk's request, copied in when the walk starts
     long long q[NS];      // local query index inside its request
     long long pbeg[NS];   // row of prev (node2vec)
     int req[NS];
@@ -879,20 +879,6 @@ __device__ __forceinline__ int find_req(const ReqDev* __restrict__ reqs, int n_r
     return lo;
 }
 
-// Served form: the ring slot of the request holding query gq.  Requests are
-// published in order with ascending q_begin; the live window is the last
-// maxr requests.
-__device__ __forceinline__ int find_ring(const ServeDev& sv, long long gq) {
-    const long long R = (long long)*sv.pub_r;
-    long long lo = R > sv.maxr ? R - sv.maxr : 0, hi = R - 1;
-    while (lo < hi) {
-        const long long mid = (lo + hi + 1) >> 1;
-        if (sv.ring[mid % sv.maxr].q_begin <= gq) lo = mid;
-        else hi = mid - 1;
-    }
-    return (int)(lo % sv.maxr);
-}
-
 // Per-warp counters, kept by lane 0 and flushed at exit.
 struct Counters {
     unsigned long long v[C_NUM];
@@ -952,9 +938,8 @@ __device__ __forceinline__ void commit(const GraphDev& g, Smem<NT>& sm, const Re
 
 // Finish the step of a hub task (the warp that completed its last segment).
 template <int MODE, int NT>
-__device__ void hub_finalize(const GraphDev& g, const ReqDev* __restrict__ reqs, Smem<NT>& sm, HubTask& H, int lane,
-                             int* win, Counters& cnt) {
-    const ReqDev& R = reqs[H.req];
+__device__ void hub_finalize(const GraphDev& g, Smem<NT>& sm, HubTask& H, int lane, int* win, Counters& cnt) {
+    const ReqDev& R = sm.rq[H.slot];
     const StepCtx c = H.c;
     int sel = -1;
     uint32_t oz = 0xFFFFFFFFu;
@@ -1028,9 +1013,8 @@ __device__ __forceinline__ bool hub_claim(Smem<NT>& sm, int lane, int& h, int& j
 // Fold a sampled segment into its hub task; the warp that completes the last
 // segment finishes the step.  Warp-collective.
 template <int MODE, int NT>
-__device__ __forceinline__ void hub_merge(const GraphDev& g, const ReqDev* __restrict__ reqs, Smem<NT>& sm,
-                                          HubTask& H, int j, const WarpRes& res, unsigned long long lane_sum,
-                                          int lane, int* win, Counters& cnt) {
+__device__ __forceinline__ void hub_merge(const GraphDev& g, Smem<NT>& sm, HubTask& H, int j, const WarpRes& res,
+                                          unsigned long long lane_sum, int lane, int* win, Counters& cnt) {
     if (MODE == MODE_FAST) {
         if (lane == 0 && res.sel >= 0)
             atomicMin(&H.best, ((unsigned long long)__float_as_uint(res.tau) << 32) | (unsigned)res.sel);
@@ -1046,7 +1030,7 @@ __device__ __forceinline__ void hub_merge(const GraphDev& g, const ReqDev* __res
     last = __shfl_sync(FULL, last, 0);
     if (last) {
         __threadfence_block();
-        hub_finalize<MODE, NT>(g, reqs, sm, H, lane, win, cnt);
+        hub_finalize<MODE, NT>(g, sm, H, lane, win, cnt);
     }
 }
 
@@ -1136,38 +1120,59 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                 // lane 0 read it once for the whole warp
                 int st = __shfl_sync(FULL, lane == 0 ? *(volatile int*)&sm.state[jj] : 0, 0);
                 if (st == ST_EMPTY && !exhausted) {
-                    // claim one query (lane 0) and initialise the slot
-                    long long gq = 0;
+                    // claim one query (lane 0): r = its request, qi = its
+                    // index inside the request; -1 if none
+                    long long qi = -1;
                     int r = 0;
                     if (serving) {
-                        // served form: take the next published query, if any
-                        gq = -1;
-                        if (lane == 0) {
+                        // served form: the oldest published request with
+                        // queries left hands out its next one; once the host
+                        // asks the engine to stop, nothing new is claimed
+                        if (lane == 0 && !*sv.stop) {
                             for (int tries = 0; tries < 64; ++tries) {
-                                const unsigned long long cq = *(volatile unsigned long long*)sv.cursor;
-                                if (cq >= *sv.pub_q) break;
-                                if (atomicCAS(sv.cursor, cq, cq + 1) == cq) {
-                                    gq = (long long)cq;
-                                    r = find_ring(sv, gq);
+                                const unsigned long long h = *(volatile unsigned long long*)sv.head;
+                                if ((long long)h >= *sv.pub_r) break;
+                                const int rs = (int)(h % (unsigned long long)sv.maxr);
+                                const unsigned long long old = atomicAdd(&sv.taken[rs], 1ull);
+                                if (old < kTakenBase) {
+                                    qi = (long long)(old + (unsigned long long)__ldcg(&sv.ring[rs].n_q) - kTakenBase);
+                                    r = rs;
                                     break;
                                 }
+                                atomicCAS(sv.head, h, h + 1);  // exhausted: move the head on
                             }
                         }
-                        gq = __shfl_sync(FULL, gq, 0);
-                        if (gq < 0) continue;  // nothing published right now: the slot stays empty
+                        qi = __shfl_sync(FULL, qi, 0);
+                        if (qi < 0) continue;  // nothing published right now: the slot stays empty
                     } else {
+                        long long gq = 0;
                         if (lane == 0) gq = (long long)atomicAdd(&scratch->cursor, 1ull);
                         gq = __shfl_sync(FULL, gq, 0);
-                        if (gq >= total) exhausted = true;
-                        else if (lane == 0) r = find_req(reqs, n_req, gq);
+                        if (gq >= total) {
+                            exhausted = true;
+                        } else if (lane == 0) {
+                            r = find_req(reqs, n_req, gq);
+                            qi = gq - reqs[r].q_begin;
+                        }
+                    }
+                    if (!exhausted) {
+                        // the walk's own copy of its request (through L2: a
+                        // served ring slot is rewritten between requests)
+                        r = __shfl_sync(FULL, r, 0);
+                        constexpr int RW = (int)(sizeof(ReqDev) / 8);
+                        static_assert(sizeof(ReqDev) % 8 == 0 && RW <= 32, "request copy: one word per lane");
+                        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(&reqs[r]);
+                        if (lane < RW)
+                            reinterpret_cast<unsigned long long*>(&sm.rq[jj])[lane] = serving ? __ldcg(src + lane)
+                                                                                               : src[lane];
+                        __syncwarp();
                     }
                     if (!exhausted && lane == 0) {
-                        const ReqDev& Rq = reqs[r];
-                        const long long qi = gq - Rq.q_begin;
-                        const int start = __ldg(Rq.starts + qi);
-                        const int pv = Rq.prev ? __ldg(Rq.prev + qi) : -1;
-                        const int t0 = Rq.step0 ? __ldg(Rq.step0 + qi) : 0;
-                        int lim = Rq.lengths ? __ldg(Rq.lengths + qi) : Rq.max_len;
+                        const ReqDev& Rq = sm.rq[jj];
+                        const int start = __ldcg(Rq.starts + qi);
+                        const int pv = Rq.prev ? __ldcg(Rq.prev + qi) : -1;
+                        const int t0 = Rq.step0 ? __ldcg(Rq.step0 + qi) : 0;
+                        int lim = Rq.lengths ? __ldcg(Rq.lengths + qi) : Rq.max_len;
                         lim = min(lim, Rq.max_len);
                         sm.q[jj] = qi;
                         sm.req[jj] = r;
@@ -1199,7 +1204,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                 }
                 if (st == ST_FINISH) {
                     // retire: path_len and -1 padding
-                    const ReqDev& Rq = reqs[sm.req[jj]];
+                    const ReqDev& Rq = sm.rq[jj];
                     const long long width = (long long)Rq.max_len + 1;
                     const int k = sm.k[jj];
                     int32_t* row = Rq.paths + sm.q[jj] * width;
@@ -1231,17 +1236,19 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                 }
             }
             if (s < 0 && !waiting && serving) {
-                // served form with nothing to do: wait for new requests, bounded
-                const unsigned long long now = global_timer_ns();
+                // served form with nothing to do: poll for new requests,
+                // backing off up to 32 us; return once the host asks to stop,
+                // or (bounded wait) after 2 s without any work
                 int quit = 0;
                 if (lane == 0) {
-                    if (*sv.stop) quit = 1;
-                    else if (idle_since == 0) idle_since = now;
-                    else if (now - idle_since > sv.idle_ns) quit = 1;
+                    const unsigned long long now = global_timer_ns();
+                    quit = *sv.stop;
+                    if (idle_since == 0) idle_since = now;
+                    else if (now - idle_since > kWaitLimitNs) quit = 1;
                 }
                 if (__shfl_sync(FULL, quit, 0)) break;
-                idle_since = __shfl_sync(FULL, idle_since, 0);
-                __nanosleep(2000);
+                __nanosleep(nap);
+                nap = min(nap * 2u, 32768u);
                 continue;
             }
             if (s < 0) {
@@ -1265,7 +1272,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
             }
 
             // ---- one step of slot s ----
-            R = &reqs[sm.req[s]];
+            R = &sm.rq[s];
             if (sm.t[s] >= sm.lim[s]) {
                 if (lane == 0) sm.state[s] = ST_FINISH;
                 __syncwarp();
@@ -1316,7 +1323,6 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                         H.seed = seed;
                         H.qid = qid;
                         H.t = t;
-                        H.req = sm.req[s];
                         sm.state[s] = ST_HUB;
                         __threadfence_block();
                         atomicExch(&H.ctl, (unsigned)H_ACTIVE << 24);
@@ -1350,7 +1356,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
 
         // ------------------------------------------------ use the result
         if (seg) {
-            hub_merge<MODE, NT>(g, reqs, sm, sm.hub[h], j, res, lane_sum, lane, win, cnt);
+            hub_merge<MODE, NT>(g, sm, sm.hub[h], j, res, lane_sum, lane, win, cnt);
             continue;
         }
         int sel = -1;
@@ -1429,12 +1435,18 @@ cudaError_t launch_serve_one(const GraphDev& g, const ServeDev& sv, Scratch* scr
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (tu.ctas_per_sm > 0) per_sm = min(per_sm, tu.ctas_per_sm);
+    // The resident engine leaves room for other kernels: one CTA slot on
+    // every SM (eight SMs when only one CTA fits).  Filling every SM would
+    // hold back other streams' kernels for as long as the server runs, and
+    // through the hardware queues streams share, the server's own copies
+    // queued behind them.
+    const long long grid = (long long)sms * per_sm - (per_sm > 1 ? sms : min(8, sms - 1));
     const int sw = max(1, min(SW_MAX, tu.slots / (NT / 32)));
     int d_t = tu.d_warp;
     if (MODE == MODE_EXACT) d_t = min(d_t, NCHUNK_MAX * 128 - 8);
     ReqTable tab;
     memset(&tab, 0, sizeof tab);
-    kern<<<(unsigned)(sms * per_sm), NT, dyn, stream>>>(g, tab, 0, 0ll, scratch, sw, d_t, 4096, sv);
+    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, tab, 0, 0ll, scratch, sw, d_t, 4096, sv);
     return cudaGetLastError();
 }
 

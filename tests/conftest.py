@@ -11,6 +11,7 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: long-running GPU test")
+    config.addinivalue_line("markers", "timeout(seconds): per-test time limit (pytest-timeout, where installed)")
 
 
 @pytest.fixture(scope="session")

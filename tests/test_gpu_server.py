@@ -12,7 +12,8 @@ import torch
 import fw_inputs as fi
 from gpu_common import cached_graph, check_valid, device_graph
 
-pytestmark = pytest.mark.gpu
+# a served run that stops making progress fails the test instead of hanging it
+pytestmark = [pytest.mark.gpu, pytest.mark.timeout(180)]
 
 ALGOS = ["weighted", "node2vec", "metapath", "ppr"]
 
@@ -84,3 +85,25 @@ def test_idle_engine_is_relaunched():
     srv.close()
     assert torch.equal(a[0], b[0])
     assert st["launches"] >= 2
+
+
+def test_ring_slots_reused_many_times():
+    """A 4-entry request ring for 40 requests: each slot is refilled about
+    ten times while the engine keeps running, and every result still equals
+    the request run alone (exact mode: bit for bit)."""
+    from paper_2404_08364_gb300 import Server
+    g = cached_graph("rmat", 14, 2)
+    dg = device_graph(g)
+    rng = np.random.default_rng(9)
+    reqs = _mix(g, 40, 303, rng)
+    srv = Server(dg, mode="exact", mem_budget=64 << 20, max_requests=4, idle_ms=50.0)
+    tickets = [srv.submit(**r) for r in reqs]
+    outs = [srv.result(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs)
+    for r, (paths, plen, _) in zip(reqs, outs):
+        alone_p, alone_l = dg.walk(r["algo"], r["starts"].cuda(), r["max_len"], r["seed"], mode="exact", p=2.0,
+                                   q=0.5, lengths=None if r["lengths"] is None else r["lengths"].cuda())
+        assert torch.equal(plen, alone_l.cpu()), r["algo"]
+        assert torch.equal(paths, alone_p.cpu()), r["algo"]
