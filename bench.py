@@ -111,6 +111,35 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+KERNEL_SOURCES = ("paper_2404_08364_gb300/csrc/fw_walk.cu", "paper_2404_08364_gb300/csrc/fw_internal.cuh")
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic_ratio(workload):
+    """DRAM bytes per algorithmic byte of the walk kernel on `workload`, from
+    an ncu capture summarised under profiles/, if that capture was taken of
+    the kernel as it is now; else None."""
+    import glob
+    import re
+    pat = re.compile(r"^traffic-per-algorithmic-byte: ([0-9.]+) \(workload (\S+), sources ([0-9a-f]+)\)")
+    cur = kernel_sources_hash()
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for line in f:
+                m = pat.match(line.strip())
+                if m and m.group(2) == workload and m.group(3) == cur:
+                    return float(m.group(1)), os.path.relpath(path, ROOT)
+    return None
+
+
 def make_graph(w, device):
     import fw_inputs as fi
     t0 = time.time()
@@ -417,6 +446,7 @@ def main():
 
     peak, peak_kind = load_peaks()
     algo_bytes_per_launch = st["algo_bytes"] / args.steps
+    prof = profiled_traffic_ratio(args.workload)
     achieved = algo_bytes_per_launch / (ms_total / args.steps / 1e3) / 1e9
     line = {
         "metric": "walk steps/s", "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -428,7 +458,12 @@ def main():
                    "parallelism": f"query shards x{world} (graph replicas)",
                    "graph_gen_s": round(gen_s, 1), "tuning": dg.get_tuning()},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": prof[0] * algo_bytes_per_launch if prof else None,
+                     "traffic_source": (f"{prof[1]}: ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
+                                        f"full-size launch per algorithmic byte ({prof[0]}), times this run's "
+                                        f"algorithmic bytes per launch") if prof else
+                                       "no ncu capture of the kernel as built now",
                      "peak_kind": f"{peak_kind} (copy bandwidth)",
                      "algo_bytes_per_launch": algo_bytes_per_launch,
                      "kernel": "walk_kernel (persistent engine)"},
