@@ -356,10 +356,13 @@ struct BBlock {
 // B's side: the stage's valid entries colS[ia, ib) are sorted, so only the B
 // values inside [colS[ia], colS[ib-1]] can match; each such value (typically
 // a handful per stage, one per lane) binary-searches the staged entries and
-// sets its bit in the warp's 256-bit mask.  A stage whose value range holds
-// more than 512 entries of B (B much denser than this part of N(cur)) is
+// sets its bit in the warp's 256-bit mask.  When the stage's value range,
+// at the density of the loaded block, would hold several more blocks of B,
+// one search finds the end of its window; if the window holds more than 512
+// entries of B (B much denser than this part of N(cur)), the stage is
 // answered from the entries' side instead, by lockstep binary searches of
-// each lane's values in B.  cv[0..3] are this lane's entries at stage
+// each lane's values in B, and the next stage continues from the largest
+// position found.  cv[0..3] are this lane's entries at stage
 // positions 4 lane + j, cv[4..7] those at 128 + 4 lane + j; bit i of the
 // result (and of `valid`) belongs to cv[i].  Warp-collective.
 __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B, int pd, BBlock& bb,
@@ -379,7 +382,7 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
     }
     if (lane < 8) mask[lane] = 0u;
     __syncwarp();
-    for (int guard = 0; guard < 4; ++guard) {
+    for (int guard = 0;; ++guard) {
         if (bb.base < 0) {
             bb.base = lower_bound_from(B, pd, 0, amin, lane);
             load_b128(B, pd, bb.base, lane, bb.v);
@@ -394,13 +397,16 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
             last = __shfl_sync(FULL, bb.v[3], 31);
         }
         if (bb.base >= pd) break;
-        if (last <= amax && guard == 0) {
-            // the stage's range runs past this block: if B is dense there,
-            // search from the entries' side
+        if (last <= amax && guard == 0 &&
+            (float)(amax - last) * 128.0f > 384.0f * (float)(last - __shfl_sync(FULL, bb.v[0], 0) + 1)) {
+            // the stage's range runs well past this block and, at the
+            // block's density, holds several more blocks of B: if B is dense
+            // there, search from the entries' side
             const int ub = lower_bound_from(B, pd, bb.base + 128, amax == INT_BIG - 1 ? INT_BIG : amax + 1, lane);
             if (ub - bb.base > 512) {
                 const int lo = bb.base;
                 unsigned f = 0;
+                int top = lo;
 #pragma unroll 1
                 for (int h = 0; h < 2; ++h) {
                     int a[4], b[4], x[4];
@@ -424,10 +430,15 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
                     }
 #pragma unroll
                     for (int j = 0; j < 4; ++j)
-                        if ((valid >> (4 * h + j) & 1u) && a[j] < ub && __ldg(B + a[j]) == x[j])
-                            f |= 1u << (4 * h + j);
+                        if (valid >> (4 * h + j) & 1u) {
+                            top = max(top, a[j]);
+                            if (a[j] < ub && __ldg(B + a[j]) == x[j]) f |= 1u << (4 * h + j);
+                        }
                 }
-                bb.base = -1;  // the next stage starts from a fresh search
+                // the next stage's entries are larger: its window starts at
+                // or after the largest position found here
+                bb.base = __reduce_max_sync(FULL, top);
+                load_b128(B, pd, bb.base, lane, bb.v);
                 return f;
             }
         }
