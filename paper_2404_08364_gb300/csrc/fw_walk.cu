@@ -350,7 +350,24 @@ __device__ __forceinline__ unsigned chunk_members(const int32_t* __restrict__ B,
 struct BBlock {
     int base;   // -1: nothing loaded yet
     int v[4];
+    int nv[4];  // the next block, B[base + 128, base + 256), already requested
 };
+
+// Load the block at `base` and request the one after it.
+__device__ __forceinline__ void bb_load(const int32_t* __restrict__ B, int pd, int base, int lane, BBlock& bb) {
+    bb.base = base;
+    load_b128(B, pd, base, lane, bb.v);
+    load_b128(B, pd, base + 128, lane, bb.nv);
+}
+
+// Move to the next block (its loads were issued a block earlier) and
+// request the one after it.
+__device__ __forceinline__ void bb_advance(const int32_t* __restrict__ B, int pd, int lane, BBlock& bb) {
+    bb.base += 128;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) bb.v[i] = bb.nv[i];
+    load_b128(B, pd, bb.base + 128, lane, bb.nv);
+}
 
 // node2vec membership for a stage of N(cur) in shared memory, driven from
 // B's side: the stage's valid entries colS[ia, ib) are sorted, so only the B
@@ -384,16 +401,14 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
     __syncwarp();
     for (int guard = 0;; ++guard) {
         if (bb.base < 0) {
-            bb.base = lower_bound_from(B, pd, 0, amin, lane);
-            load_b128(B, pd, bb.base, lane, bb.v);
+            bb_load(B, pd, lower_bound_from(B, pd, 0, amin, lane), lane, bb);
         }
         // (a step normally starts with B's first block already requested by
         // the caller, overlapping that load with the first stage's copy)
         int last = __shfl_sync(FULL, bb.v[3], 31);
         if (last < amin) {
             // the whole block lies below this stage: jump to the stage's range
-            bb.base = lower_bound_from(B, pd, bb.base + 128, amin, lane);
-            load_b128(B, pd, bb.base, lane, bb.v);
+            bb_load(B, pd, lower_bound_from(B, pd, bb.base + 128, amin, lane), lane, bb);
             last = __shfl_sync(FULL, bb.v[3], 31);
         }
         if (bb.base >= pd) break;
@@ -437,8 +452,7 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
                 }
                 // the next stage's entries are larger: its window starts at
                 // or after the largest position found here
-                bb.base = __reduce_max_sync(FULL, top);
-                load_b128(B, pd, bb.base, lane, bb.v);
+                bb_load(B, pd, __reduce_max_sync(FULL, top), lane, bb);
                 return f;
             }
         }
@@ -457,9 +471,11 @@ __device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B
         }
         if (last > amax) break;  // the block reaches past the stage: keep it for the next one
         // every entry of the block is at most amax: move on to the next block
-        bb.base += 128;
-        if (bb.base >= pd) break;
-        load_b128(B, pd, bb.base, lane, bb.v);
+        if (bb.base + 128 >= pd) {
+            bb.base += 128;
+            break;
+        }
+        bb_advance(B, pd, lane, bb);
     }
     __syncwarp();
     const int sh = (lane & 7) * 4;
@@ -763,8 +779,7 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
     if (n2v && qa == ((c.beg >> 2) & ~3ll)) {
         // a whole row (or its first segment): start loading N(prev)'s first
         // block now, while the first stage is still on its way
-        bb.base = 0;
-        load_b128(g.col + c.pbeg, c.pdeg, 0, lane, bb.v);
+        bb_load(g.col + c.pbeg, c.pdeg, 0, lane, bb);
     }
     bool ok = true;
     for (int k = 0; k < nst; ++k) {
