@@ -41,13 +41,24 @@ WORKLOADS = {
                             batch_log2=22, slices=1),
     "rmat25_weighted": dict(scale=25, algo="weighted", p=1.0, q=1.0, mode="fast", L=80, types=None,
                             batch_log2=22, slices=8),
+    # extra distributions: log-normal weights (Appendix C.1, sigma = 3) and
+    # the paper's PPR workload, every query from the max-degree vertex
+    "rmat22_weighted_lognormal3": dict(scale=22, algo="weighted", p=1.0, q=1.0, mode="fast", L=80, types=None,
+                                       batch_log2=20, slices=4, weights="lognormal3"),
+    "rmat22_ppr_maxdeg": dict(scale=22, algo="ppr", p=1.0, q=1.0, mode="fast", L=100, types=None,
+                              batch_log2=20, slices=1, starts="maxdeg"),
 }
 
 
 def describe(w):
-    return (f"{w['algo']} p={w['p']:g} q={w['q']:g}, {w['mode']} mode, R-MAT scale {w['scale']} "
-            f"(a,b,c=.57,.19,.19, ef 16, symmetrised), L={w['L']}, "
-            f"{2 ** w['batch_log2']} queries per step (1/{w['slices']} of one query per vertex)")
+    wt = w.get("weights", "grid14")
+    wdesc = "weights [1,5) on a 2^-14 grid" if wt == "grid14" else f"log-normal weights sigma={wt[len('lognormal'):]}"
+    sdesc = ("every query from the max-degree vertex" if w.get("starts") == "maxdeg"
+             else f"1/{w['slices']} of one query per vertex")
+    algo = "PPR stop 0.2" if w["algo"] == "ppr" else f"{w['algo']} p={w['p']:g} q={w['q']:g}"
+    return (f"{algo}, {w['mode']} mode, R-MAT scale {w['scale']} "
+            f"(a,b,c=.57,.19,.19, ef 16, symmetrised, {wdesc}), L={w['L']}, "
+            f"{2 ** w['batch_log2']} queries per step ({sdesc})")
 
 
 def load_peaks():
@@ -143,12 +154,15 @@ def profiled_traffic_ratio(workload):
 def make_graph(w, device):
     import fw_inputs as fi
     t0 = time.time()
-    g = fi.rmat(w["scale"], types_seed=w["types"], device=device)
+    g = fi.rmat(w["scale"], types_seed=w["types"], weights=w.get("weights", "grid14"), device=device)
     return g, time.time() - t0
 
 
-def slice_starts(n, k, slices, batch, device):
+def slice_starts(n, k, slices, batch, device, w=None, g=None):
     import torch
+    if w is not None and w.get("starts") == "maxdeg":
+        deg = g.row_ptr[1:] - g.row_ptr[:-1]
+        return torch.full((batch,), int(torch.argmax(deg)), dtype=torch.int32, device=device)
     s = torch.arange(k % slices, n, slices, dtype=torch.int32, device=device)
     return s[:batch]
 
@@ -171,9 +185,16 @@ def cpu_oracle_sample(g_host, w, seconds=15.0, threads=None, seed=42):
     t0 = time.time()
     stride = max(1, n // 100003)
 
+    hub = None
+    if w.get("starts") == "maxdeg":
+        hub = int(np.argmax(np.diff(g_host.row_ptr.numpy())))
+
     def run(ci):
-        st = np.arange(ci * per_call * stride, (ci + 1) * per_call * stride, stride, dtype=np.int32) % n
-        _, plen = oracle.walk_exact(csr, w["algo"], prm, st, w["L"], seed, q0=int(st[0]))
+        if hub is not None:
+            st = np.full(per_call, hub, dtype=np.int32)
+        else:
+            st = np.arange(ci * per_call * stride, (ci + 1) * per_call * stride, stride, dtype=np.int32) % n
+        _, plen = oracle.walk_exact(csr, w["algo"], prm, st, w["L"], seed, q0=ci * per_call)
         return int((plen - 1).sum())
 
     with cf.ThreadPoolExecutor(max_workers=threads) as ex:
@@ -192,8 +213,9 @@ def cpu_oracle_sample(g_host, w, seconds=15.0, threads=None, seed=42):
             total_steps += f.result()
             calls += 1
     dt = time.time() - t0
+    where = "every start at the max-degree vertex" if hub is not None else "starts spread over the vertex range"
     desc = (f"oracle (exact-mode C walker) on {calls * per_call} queries of the same workload "
-            f"(starts spread over the vertex range), {threads} threads, {dt:.1f} s")
+            f"({where}), {threads} threads, {dt:.1f} s")
     return total_steps / dt, threads, desc
 
 
@@ -319,6 +341,109 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
+def run_sweep(args):
+    """Scalability (Appendix C.5): throughput in scanned CSR
+    entries (edges) per second on an R-MAT graph, (a) against the number of
+    queries 10^2..10^7 at length 80, (b) against the length 10..80 at 10^6
+    queries; random starts; one warm-up launch, then one timed launch per
+    point (CUDA events on the launching stream)."""
+    import torch
+
+    import fw_inputs as fi
+    from paper_2404_08364_gb300.build import build
+    build()
+    from paper_2404_08364_gb300 import DeviceGraph
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    scale = args.sweep_scale
+    g = fi.rmat(scale, device=dev)
+    dg = DeviceGraph.from_tensors(g.row_ptr, g.col, g.w_f32, None, None, borrow=True, device=dev)
+    algo, p, q = {"node2vec": ("node2vec", 1.0, 2.0), "weighted": ("weighted", 1.0, 1.0)}[args.sweep_algo]
+    stream = torch.cuda.current_stream(dev)
+    points = [(10 ** e, 80) for e in range(2, 8)] + [(10 ** 6, L) for L in (10, 20, 40)]
+    rows = []
+    for nq, L in points:
+        starts = fi.random_starts(g.n, nq, 4242).to(dev)
+        paths = torch.empty((nq, L + 1), dtype=torch.int32, device=dev)
+        plen = torch.empty(nq, dtype=torch.int32, device=dev)
+        dg.walk(algo, starts, L, 7, mode="fast", p=p, q=q, paths=paths, path_len=plen, stream=stream)
+        torch.cuda.synchronize(dev)
+        dg.stats_reset(stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dg.walk(algo, starts, L, 8, mode="fast", p=p, q=q, q_id0=nq, paths=paths, path_len=plen, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        s = e0.elapsed_time(e1) / 1e3
+        st = dg.stats()
+        rows.append({"queries": nq, "length": L, "edges_per_s": st["rows_scanned"] / s,
+                     "steps_per_s": st["steps"] / s, "ms": s * 1e3})
+        del paths, plen
+    out = {"metric": "edges/s (scanned CSR entries per second)", "unit": "edges/s", "higher_is_better": True,
+           "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{algo} p={p:g} q={q:g}, fast mode, R-MAT scale {scale} "
+                                  f"(a,b,c=.57,.19,.19, ef 16, symmetrised), random starts",
+                      "tuning": dg.get_tuning()},
+           "sweep": rows}
+    print(json.dumps(out), flush=True)
+    dg.free()
+
+
+def run_batched(args):
+    """Out-of-memory batches (Section 5.2, Eq. 3): node2vec p=1 q=2 on R-MAT
+    with host inputs and outputs through fw_walk_batched, the byte budget set
+    so the queries take `--batches` batches, against one device-resident
+    launch of the same queries followed by the copy of its paths to the host."""
+    import torch
+
+    import fw_inputs as fi
+    from paper_2404_08364_gb300.build import build
+    build()
+    from paper_2404_08364_gb300 import DeviceGraph
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    scale, L = args.sweep_scale, 80
+    g = fi.rmat(scale, device=dev)
+    dg = DeviceGraph.from_tensors(g.row_ptr, g.col, g.w_f32, None, None, borrow=True, device=dev)
+    nq = 1 << 22
+    starts = fi.random_starts(g.n, nq, 99)
+    per_query = (L + 3) * 4
+    budget = 2 * per_query * ((nq + args.batches - 1) // args.batches)
+    hp = torch.empty((nq, L + 1), dtype=torch.int32).pin_memory()
+    hl = torch.empty(nq, dtype=torch.int32).pin_memory()
+    kw = dict(mode="fast", p=1.0, q=2.0)
+    dg.walk_batched("node2vec", starts[:4096], L, 1, budget_bytes=budget, **kw)  # warm-up
+    dg.stats_reset()
+    t0 = time.perf_counter()
+    _, _, bq = dg.walk_batched("node2vec", starts, L, 2, budget_bytes=budget, paths=hp, path_len=hl, **kw)
+    t_b = time.perf_counter() - t0
+    steps_b = dg.stats()["steps"]
+    ds = starts.to(dev)
+    dp = torch.empty((nq, L + 1), dtype=torch.int32, device=dev)
+    dl = torch.empty(nq, dtype=torch.int32, device=dev)
+    torch.cuda.synchronize(dev)
+    dg.stats_reset()
+    t0 = time.perf_counter()
+    dg.walk("node2vec", ds, L, 2, paths=dp, path_len=dl, **kw)
+    hp.copy_(dp)
+    hl.copy_(dl)
+    torch.cuda.synchronize(dev)
+    t_1 = time.perf_counter() - t0
+    steps_1 = dg.stats()["steps"]
+    out = {"metric": "walk steps/s, host outputs", "unit": "steps/s", "higher_is_better": True, "n_gpus": 1,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"node2vec p=1 q=2, fast mode, R-MAT scale {scale}, L={L}, {nq} random starts, "
+                                  f"host (pinned) outputs of {nq * (L + 1) * 4 / 1e9:.2f} GB",
+                      "budget_bytes": budget, "queries_per_batch": bq, "batches": (nq + bq - 1) // bq},
+           "batched_steps_per_s": steps_b / t_b, "batched_s": t_b,
+           "one_launch_then_copy_steps_per_s": steps_1 / t_1, "one_launch_then_copy_s": t_1,
+           "batched_over_one_launch": (steps_b / t_b) / (steps_1 / t_1)}
+    print(json.dumps(out), flush=True)
+    dg.free()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -334,6 +459,11 @@ def main():
     ap.add_argument("--slots", type=int, default=0, help="walk slots per CTA (0 = default)")
     ap.add_argument("--d-t", type=int, default=0, help="hub threshold d_t (0 = default)")
     ap.add_argument("--serve", action="store_true", help="served-form benchmark (config 5) instead")
+    ap.add_argument("--sweep", action="store_true", help="scalability sweep (edges/s vs queries and length)")
+    ap.add_argument("--sweep-scale", type=int, default=22)
+    ap.add_argument("--sweep-algo", default="node2vec", choices=["node2vec", "weighted"])
+    ap.add_argument("--batched", action="store_true", help="out-of-memory batches on two streams (Eq. 3)")
+    ap.add_argument("--batches", type=int, default=8)
     ap.add_argument("--serve-scale", type=int, default=24)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-mem-mb", type=int, default=2048)
@@ -348,6 +478,10 @@ def main():
         return run_reference(args, w)
     if args.serve:
         return run_serve(args)
+    if args.sweep:
+        return run_sweep(args)
+    if args.batched:
+        return run_batched(args)
 
     import torch
     import torch.distributed as dist
@@ -379,7 +513,7 @@ def main():
     steps_total = args.warmup + args.steps
     starts = []
     for k in range(steps_total):
-        s = slice_starts(g.n, k, w["slices"], batch * world, dev)
+        s = slice_starts(g.n, k, w["slices"], batch * world, dev, w, g)
         b, e = shard_range(s.numel(), rank, world)
         starts.append((s[b:e].contiguous(), (k % w["slices"]) * (g.n // w["slices"]) + b))
     paths = torch.empty((batch, w["L"] + 1), dtype=torch.int32, device=dev)

@@ -117,6 +117,21 @@ def _attributes(src, dst, seed: int, weights: str, types_seed: Optional[int]):
         wu = 16384 + k
         w_u32 = wu.to(torch.int32)
         w_f32 = (wu.to(torch.float64) / 16384.0).to(torch.float32)
+    elif weights.startswith("lognormal"):
+        # log-normal weights, mean 0 and standard deviation sigma of the log
+        # (Appendix C.1's sweep, sigma = 1..3): Z by Box-Muller from two
+        # hashed uniforms, the integer weight round(e^(sigma Z) * 2^14) >= 1,
+        # the float that integer times 2^-14 (to FP32 rounding).  float64
+        # exp/log/cos may differ in the last bit between CPU and GPU, so this
+        # recipe is reproducible per device only.
+        sigma = float(weights[len("lognormal"):])
+        h2 = _hash2(seed * 2 + 3, lo, hi)
+        u1 = (h.to(torch.float64) + 0.5) / 4294967296.0
+        u2 = (h2.to(torch.float64) + 0.5) / 4294967296.0
+        z = torch.sqrt(-2.0 * torch.log(u1)) * torch.cos(2.0 * math.pi * u2)
+        wu = torch.clamp(torch.round(torch.exp(sigma * z) * 16384.0), 1.0, 2147483647.0).to(torch.int64)
+        w_u32 = wu.to(torch.int32)
+        w_f32 = (wu.to(torch.float64) / 16384.0).to(torch.float32)
     else:
         raise ValueError(f"unknown weights recipe {weights!r}")
     etype = None

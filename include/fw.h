@@ -226,6 +226,33 @@ int fw_walk_multi(fw_graph* g, const fw_request* reqs, int32_t n_req, void* stre
 #define FW_NOALLOC_MAX_REQS 1024
 int fw_walk_noalloc(fw_graph* g, const fw_request* reqs, int32_t n_req, void* stream);
 
+/*
+ * fw_walk_batched — walks whose results exceed device memory (Section 5.2,
+ * Fig. 8 and Eq. 3).  The n_q queries are cut into batches of
+ *     |P_G| = floor(budget_bytes / (2 * (max_len + 3) * 4))
+ * queries: Eq. 3 with budget_bytes standing for M - M_G, its (L_max + 1)
+ * result words per query plus each query's start and path length.  Batches
+ * alternate between two streams, each with its own result pool, query cursor
+ * and counters, so one batch's paths are copied to the host while the next
+ * batch walks.  budget_bytes = 0 takes the free device memory less 256 MiB.
+ *   h_starts [n_q], h_lengths [n_q] or NULL, h_paths [n_q][max_len + 1],
+ *   h_path_len [n_q]: host memory (pinned memory lets the copies overlap the
+ *   walks; pageable memory works without overlap).  Output layout, padding
+ *   and random counters (q_id0 + query index) are those of fw_walk_ex, so the
+ *   paths equal one launch over all queries.
+ *   batch_q (may be NULL) receives |P_G| as used (at most n_q).
+ * Synchronous; the work is added to the graph's counters (fw_stats).
+ * Errors: FW_EINVAL (arguments, parameters), FW_ENOMEM (the budget does not
+ * hold one query in each pool, or an allocation failed), FW_ECUDA,
+ * FW_ETIMEOUT (a device wait gave up).
+ */
+int fw_walk_batched(fw_graph* g, int32_t algo, const fw_params* p, const int32_t* h_starts, int64_t n_q,
+                    const int32_t* h_lengths, int32_t max_len, uint64_t seed, int64_t q_id0,
+                    uint64_t budget_bytes, int32_t* h_paths, int32_t* h_path_len, int64_t* batch_q);
+
+/* Eq. 3's batch size for a byte budget (host arithmetic only; no GPU needed). */
+int64_t fw_batch_size(uint64_t budget_bytes, int32_t max_len);
+
 /* Same as fw_walk with an explicit query-id offset q_id0 (for sharding one
  * query range over several calls or devices with identical results). */
 int fw_walk_ex(fw_graph* g, int32_t algo, const fw_params* p, const int32_t* starts, int64_t n_q,

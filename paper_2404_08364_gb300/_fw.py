@@ -73,6 +73,10 @@ SIGNATURES = {
                                   ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64, _P, _P, _P, _P, _P]),
     "fw_walk_multi": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.c_int32, _P]),
     "fw_walk_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(Request), ctypes.c_int32, _P]),
+    "fw_walk_batched": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(Params), _P, ctypes.c_int64, _P,
+                                       ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint64, _P, _P,
+                                       ctypes.POINTER(ctypes.c_int64)]),
+    "fw_batch_size": (ctypes.c_int64, [ctypes.c_uint64, ctypes.c_int32]),
     "fw_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(Tuning)]),
     "fw_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(Tuning)]),
     "fw_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),

@@ -391,6 +391,10 @@ int make_request(const fw_graph* g, const fw_request& q, ReqDev* out) {
     return make_req(g, q.algo, &q.params, q.max_len, q.seed, out);
 }
 
+Scratch* graph_scratch(const fw_graph* g) { return g->scratch; }
+
+std::mutex& graph_mutex(fw_graph* g) { return g->mu; }
+
 }  // namespace fw
 
 extern "C" int fw_walk_ex(fw_graph* G, int32_t algo, const fw_params* p, const int32_t* starts, int64_t n_q,

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "fw.h"
 
 namespace fw {
@@ -168,5 +170,7 @@ Tuning sanitize_tuning(Tuning t);
 int set_error(int status, const char* msg);                          // records the message, returns status
 int graph_device_view(const fw_graph* g, GraphDev* out, int* device, Tuning* tuning);
 int make_request(const fw_graph* g, const fw_request& q, ReqDev* out);  // parameters only
+Scratch* graph_scratch(const fw_graph* g);                            // the graph's cursor and counters
+std::mutex& graph_mutex(fw_graph* g);                                 // serialises launches on the graph
 
 }  // namespace fw

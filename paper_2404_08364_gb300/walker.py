@@ -97,6 +97,28 @@ class DeviceGraph:
                                        _ptr(path_len), sh))
         return paths, path_len
 
+    def walk_batched(self, algo, starts, max_len: int, seed: int, mode="exact", p=1.0, q=1.0, scale=2,
+                     schema: Sequence[int] = (0, 1, 2, 3, 4), ppr_stop=0.2, lengths=None, q_id0: int = 0,
+                     budget_bytes: int = 0, paths=None, path_len=None):
+        """Walks whose results may exceed device memory (fw_walk_batched):
+        host inputs and outputs, batches of Eq. 3's size on two streams.
+        Returns (paths, path_len, queries per batch); outputs are pinned host
+        tensors unless given."""
+        algo = _fw.ALGOS.get(algo, algo)
+        prm = _fw.make_params(mode, p, q, scale, schema, ppr_stop)
+        st = _i32(torch.as_tensor(starts), "cpu")
+        n_q = st.numel()
+        if paths is None:
+            paths = torch.empty((n_q, max_len + 1), dtype=torch.int32).pin_memory()
+        if path_len is None:
+            path_len = torch.empty(n_q, dtype=torch.int32).pin_memory()
+        ln = _i32(lengths, "cpu")
+        bq = ctypes.c_int64()
+        _fw.check(_fw.lib().fw_walk_batched(self._h, algo, ctypes.byref(prm), _ptr(st), n_q, _ptr(ln), max_len,
+                                            seed & 0xFFFFFFFFFFFFFFFF, q_id0, int(budget_bytes), _ptr(paths),
+                                            _ptr(path_len), ctypes.byref(bq)))
+        return paths, path_len, bq.value
+
     def _requests(self, requests):
         arr = (_fw.Request * len(requests))()
         outs, keep = [], []

@@ -48,3 +48,17 @@ def test_missing_library_fails_loudly(tmp_path):
             _fw.lib(str(tmp_path / "nope.so"))
     finally:
         _fw._lib = saved
+
+
+def test_batch_size_follows_eq3():
+    """Eq. 3 (Section 5.2): two result pools of |P_G| queries fit in the
+    budget and two of |P_G| + 1 do not; a query needs its L + 1 path words
+    plus its start and its path length (4 bytes each)."""
+    from paper_2404_08364_gb300 import _fw
+    L = _fw.lib()
+    for budget, max_len in [(0, 80), (1, 0), (10 ** 9, 80), (123456789, 999), (2 ** 40, 80), (2 ** 20, 3)]:
+        P = L.fw_batch_size(budget, max_len)
+        per_query = (max_len + 1) * 4 + 4 + 4
+        assert 2 * P * per_query <= budget
+        assert 2 * (P + 1) * per_query > budget
+    assert L.fw_batch_size(10 ** 6, -1) == 0

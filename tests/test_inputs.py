@@ -1,5 +1,6 @@
 """The seeded input generators: determinism, CSR invariants, recipe facts."""
 
+import pytest
 import torch
 
 import fw_inputs as fi
@@ -52,3 +53,17 @@ def test_starts_and_lengths():
     assert torch.equal(s, fi.random_starts(1000, 5000, 7))
     ln = fi.uniform_lengths(5000, 10, 80, 3)
     assert int(ln.min()) == 10 and int(ln.max()) == 80
+
+
+@pytest.mark.parametrize("sigma", [1, 3])
+def test_lognormal_weights(sigma):
+    """log w has mean 0 and standard deviation sigma (Appendix C.1's weights);
+    the integer weight is at least 1 and the float is it times 2^-14."""
+    g = fi.rmat(12, weights=f"lognormal{sigma}")
+    wu = g.w_u32.to(torch.int64)
+    assert int(wu.min()) >= 1
+    lw = torch.log(wu.double() / 16384.0)
+    assert abs(float(lw.mean())) < 0.05
+    assert abs(float(lw.std()) - sigma) < 0.05 * sigma
+    rel = (g.w_f32.double() - wu.double() / 16384.0).abs() / (wu.double() / 16384.0)
+    assert float(rel.max()) <= 2.0 ** -24
