@@ -444,6 +444,43 @@ def run_batched(args):
     dg.free()
 
 
+def run_samplers(args):
+    """Section 4's samplers side by side (fw_sampler_run): DPRS (Alg. 3), ZPRS
+    (Alg. 4) and the engine's exponential-jump reservoir, at warp and CTA
+    width, over sampling sizes 2^0..2^20 (Section 6.3's sampling-size sweep).
+    Weights [1, 5) on the 2^-14 grid; enough independent draws per launch to
+    fill the GPU; the array stays in L2, so this times the samplers' own
+    work, not DRAM."""
+    import torch
+
+    from paper_2404_08364_gb300.build import build
+    build()
+    from paper_2404_08364_gb300 import sample
+
+    torch.cuda.set_device(0)
+    rows = []
+    for e in range(0, 21):
+        n = 1 << e
+        k = torch.arange(n, dtype=torch.int64)
+        w = (1.0 + ((k * 2654435761) % 65536).double() / 16384.0).float().cuda()
+        for width in (32, 256):
+            reps = max(152 * (64 if width == 32 else 8), min(1 << 22, (1 << 27) // n))
+            out = torch.empty(reps, dtype=torch.int32, device="cuda")
+            res = {}
+            for m in ("expj", "dprs", "zprs"):
+                sample(m, w, min(reps, 4096), seed=1, width=width, out=out[:min(reps, 4096)])  # warm-up
+                _, ms = sample(m, w, reps, seed=2, width=width, out=out)
+                res[m] = {"draws_per_s": reps / (ms / 1e3), "elements_per_s": reps * n / (ms / 1e3), "ms": ms}
+            best = max(res, key=lambda m: res[m]["draws_per_s"])
+            rows.append({"n": n, "width": width, "reps": reps, "best": best, **{m: res[m] for m in res}})
+    out = {"metric": "weighted draws per second", "unit": "draws/s", "higher_is_better": True, "n_gpus": 1,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "one weight array of n entries ([1,5) on a 2^-14 grid), independent draws, "
+                                  "samplers: expj (engine), dprs (Alg. 3), zprs (Alg. 4)"},
+           "sweep": rows}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -463,6 +500,7 @@ def main():
     ap.add_argument("--sweep-scale", type=int, default=22)
     ap.add_argument("--sweep-algo", default="node2vec", choices=["node2vec", "weighted"])
     ap.add_argument("--batched", action="store_true", help="out-of-memory batches on two streams (Eq. 3)")
+    ap.add_argument("--samplers", action="store_true", help="DPRS / ZPRS / engine reservoir, sampling-size sweep")
     ap.add_argument("--batches", type=int, default=8)
     ap.add_argument("--serve-scale", type=int, default=24)
     ap.add_argument("--serve-requests", type=int, default=400)
@@ -482,6 +520,8 @@ def main():
         return run_sweep(args)
     if args.batched:
         return run_batched(args)
+    if args.samplers:
+        return run_samplers(args)
 
     import torch
     import torch.distributed as dist

@@ -253,6 +253,22 @@ int fw_walk_batched(fw_graph* g, int32_t algo, const fw_params* p, const int32_t
 /* Eq. 3's batch size for a byte budget (host arithmetic only; no GPU needed). */
 int64_t fw_batch_size(uint64_t budget_bytes, int32_t max_len);
 
+/*
+ * fw_sampler_run — the parallel weighted samplers side by side (Section 4):
+ *   method 0  the engine's exponential-jump reservoir (its fast mode),
+ *   method 1  DPRS, direct parallel reservoir sampling (Alg. 3),
+ *   method 2  ZPRS, zig-zag parallel reservoir sampling (Alg. 4),
+ * each run by a group of `width` threads (32: a warp; 256: a CTA).  `reps`
+ * independent draws from the same weights d_w [n] (device, n in [1, 2^31),
+ * weights >= 0) run at once, one per group; d_out [reps] (device) receives the
+ * drawn indices (-1 if every weight is 0).  Draw r uses random counters of
+ * its own (seed, r), so the draws are independent, each with law
+ * w_i / sum(w).  If ms is not NULL the call waits and stores the launch time
+ * (CUDA events on `stream`).  Errors: FW_EINVAL (arguments), FW_ECUDA.
+ */
+int fw_sampler_run(int32_t method, int32_t width, const float* d_w, int64_t n, int64_t reps, uint64_t seed,
+                   int32_t* d_out, void* stream, float* ms);
+
 /* Same as fw_walk with an explicit query-id offset q_id0 (for sharding one
  * query range over several calls or devices with identical results). */
 int fw_walk_ex(fw_graph* g, int32_t algo, const fw_params* p, const int32_t* starts, int64_t n_q,

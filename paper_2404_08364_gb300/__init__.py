@@ -6,7 +6,7 @@ binding.  Importing the package does not load the library; the first use of
 ``DeviceGraph`` does, and raises if it is missing.
 """
 
-__all__ = ["DeviceGraph", "Server", "build"]
+__all__ = ["DeviceGraph", "Server", "sample", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -15,7 +15,7 @@ def build(force: bool = False) -> str:
 
 
 def __getattr__(name):
-    if name in ("DeviceGraph", "Server"):
+    if name in ("DeviceGraph", "Server", "sample"):
         from . import walker
         return getattr(walker, name)
     raise AttributeError(name)

@@ -77,6 +77,8 @@ SIGNATURES = {
                                        ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint64, _P, _P,
                                        ctypes.POINTER(ctypes.c_int64)]),
     "fw_batch_size": (ctypes.c_int64, [ctypes.c_uint64, ctypes.c_int32]),
+    "fw_sampler_run": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int64, ctypes.c_int64,
+                                      ctypes.c_uint64, _P, _P, ctypes.POINTER(ctypes.c_float)]),
     "fw_set_tuning": (ctypes.c_int, [_P, ctypes.POINTER(Tuning)]),
     "fw_get_tuning": (ctypes.c_int, [_P, ctypes.POINTER(Tuning)]),
     "fw_stats": (ctypes.c_int, [_P, ctypes.POINTER(Stats)]),

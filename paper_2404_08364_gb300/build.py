@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfw.so")
-SOURCES = ["fw_api.cu", "fw_walk.cu", "fw_server.cu", "fw_tune.cu", "fw_batch.cu"]
+SOURCES = ["fw_api.cu", "fw_walk.cu", "fw_server.cu", "fw_tune.cu", "fw_batch.cu", "fw_samplers.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",

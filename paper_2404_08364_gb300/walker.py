@@ -343,3 +343,23 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+SAMPLERS = {"expj": 0, "dprs": 1, "zprs": 2}
+
+
+def sample(method: str, weights, reps: int, seed: int = 1, width: int = 32, out=None, stream=None, timed=True):
+    """reps independent weighted draws from one weight vector (fw_sampler_run):
+    method "expj" (the engine's reservoir), "dprs" (Alg. 3) or "zprs"
+    (Alg. 4), by groups of `width` threads (32 or 256).  weights: float32
+    CUDA tensor.  Returns (indices int32 CUDA tensor, launch ms or None)."""
+    w = weights.contiguous()
+    if w.dtype != torch.float32 or w.device.type != "cuda":
+        raise ValueError("weights must be a float32 CUDA tensor")
+    if out is None:
+        out = torch.empty(int(reps), dtype=torch.int32, device=w.device)
+    ms = ctypes.c_float()
+    _fw.check(_fw.lib().fw_sampler_run(SAMPLERS[method], int(width), _ptr(w), w.numel(), int(reps),
+                                       seed & 0xFFFFFFFFFFFFFFFF, _ptr(out), _stream_handle(stream),
+                                       ctypes.byref(ms) if timed else None))
+    return out, (ms.value if timed else None)
