@@ -80,7 +80,10 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # raw samples: FW_CLOCKS_DIR if set, else the temp directory (the
+        # bench line carries their summary)
+        import tempfile
+        self.path = os.path.join(os.environ.get("FW_CLOCKS_DIR", tempfile.gettempdir()), f"clocks_gpu{gpu_index}.csv")
 
     def start(self):
         try:
