@@ -1,0 +1,41 @@
+"""bench.py bookkeeping on the host: the DRAM-traffic ratio from a committed
+ncu summary applies only to the workload and kernel sources it was captured
+on, and every workload line describes its inputs."""
+
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_traffic_ratio_tied_to_sources(tmp_path, monkeypatch):
+    cur = bench.kernel_sources_hash()
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "x.md").write_text(
+        "text\ntraffic-per-algorithmic-byte: 1.5 (workload wl_a, sources %s)\n"
+        "traffic-per-algorithmic-byte: 9.0 (workload wl_b, sources 0000000000000000)\n" % cur)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # the sources are hashed from ROOT: point it back at the repository for them
+    monkeypatch.setattr(bench, "kernel_sources_hash", lambda: cur)
+    assert bench.profiled_traffic_ratio("wl_a")[0] == 1.5
+    assert bench.profiled_traffic_ratio("wl_b") is None      # captured on other sources
+    assert bench.profiled_traffic_ratio("wl_c") is None      # never captured
+
+
+def test_source_hash_is_stable_and_short():
+    h = bench.kernel_sources_hash()
+    assert h == bench.kernel_sources_hash() and len(h) == 16
+
+
+def test_workloads_describe_their_inputs():
+    for name, w in bench.WORKLOADS.items():
+        d = bench.describe(w)
+        assert f"R-MAT scale {w['scale']}" in d and f"L={w['L']}" in d, name
+        if w.get("weights", "grid14").startswith("lognormal"):
+            assert "log-normal" in d
+        if w.get("starts") == "maxdeg":
+            assert "max-degree" in d
