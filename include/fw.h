@@ -39,7 +39,7 @@ typedef enum {
     FW_ENOMEM = -2,     /* device or host allocation failed */
     FW_ECUDA = -3,      /* a CUDA call or a kernel failed */
     FW_EUNSORTED = -4,  /* a CSR row is not strictly ascending */
-    FW_ETIMEOUT = -5,   /* a bounded device wait ran out (served form) */
+    FW_ETIMEOUT = -5,   /* a bounded device wait ran out (a copy or a hub task never completed) */
     FW_EBUSY = -6       /* resource in use (served form: no admission room) */
 } fw_status;
 
