@@ -66,7 +66,10 @@ typedef enum {
 #define FW_BORROW 2u        /* inputs are device pointers the caller keeps alive
                                until fw_free; nothing is copied.  Each must be
                                16-byte aligned. */
-#define FW_NO_VALIDATE 4u   /* skip the CSR checks below */
+#define FW_NO_VALIDATE 4u   /* accept unsorted rows and invalid weights (results
+                               are then undefined, but every access stays in
+                               bounds); offsets and column ranges are always
+                               checked, since the kernels index by them */
 
 typedef struct fw_graph fw_graph;
 

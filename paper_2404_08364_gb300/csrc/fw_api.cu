@@ -258,16 +258,17 @@ extern "C" int fw_load_csr(fw_graph** out, int64_t n, int64_t m, const int64_t* 
     }
     G->d_max = (int64_t)co.d_max;
     G->max_w_u32 = co.max_w_u32;
-    if (!(flags & FW_NO_VALIDATE)) {
-        if (ends[0] != 0 || ends[1] != m || (co.flags & V_ROWPTR)) rc = fail(FW_EINVAL, "fw_load_csr: row_ptr not monotone from 0 to m");
-        else if (co.flags & V_COLRANGE) rc = fail(FW_EINVAL, "fw_load_csr: column index out of [0, n)");
-        else if (co.flags & V_UNSORTED) rc = fail(FW_EUNSORTED, "fw_load_csr: a row is not strictly ascending");
+    // offsets and column ranges are always enforced: the kernels index by them
+    if (ends[0] != 0 || ends[1] != m || (co.flags & V_ROWPTR)) rc = fail(FW_EINVAL, "fw_load_csr: row_ptr not monotone from 0 to m");
+    else if (co.flags & V_COLRANGE) rc = fail(FW_EINVAL, "fw_load_csr: column index out of [0, n)");
+    else if (!(flags & FW_NO_VALIDATE)) {
+        if (co.flags & V_UNSORTED) rc = fail(FW_EUNSORTED, "fw_load_csr: a row is not strictly ascending");
         else if (co.flags & V_WF32) rc = fail(FW_EINVAL, "fw_load_csr: w_f32 has a non-positive or non-finite weight");
         else if (co.flags & V_WU32) rc = fail(FW_EINVAL, "fw_load_csr: w_u32 has a zero weight");
-        if (rc != FW_OK) {
-            release(G);
-            return rc;
-        }
+    }
+    if (rc != FW_OK) {
+        release(G);
+        return rc;
     }
     *out = G;
     return FW_OK;
