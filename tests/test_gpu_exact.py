@@ -137,6 +137,14 @@ def test_validation_errors():
     with pytest.raises(_fw.FwError) as e:
         DeviceGraph.from_tensors(rp, g.col, wz, g.w_u32)
     assert e.value.status == _fw.FW_EINVAL
+    # without validation an unsorted row loads (its results are undefined) ...
+    DeviceGraph.from_tensors(rp, bad, g.w_f32, g.w_u32, validate=False).free()
+    # ... but offsets and column ranges, which the kernels index by, are always checked
+    oob = g.col.clone()
+    oob[0] = g.n
+    with pytest.raises(_fw.FwError) as e:
+        DeviceGraph.from_tensors(rp, oob, g.w_f32, g.w_u32, validate=False)
+    assert e.value.status == _fw.FW_EINVAL
     dg = device_graph(g)
     with pytest.raises(_fw.FwError):
         dg.walk("node2vec", torch.zeros(4, dtype=torch.int32), 5, 1, p=3.0, q=0.5)  # 2/3 not integral
