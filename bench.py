@@ -508,7 +508,7 @@ def main():
     ap.add_argument("--serve-scale", type=int, default=24)
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-mem-mb", type=int, default=2048)
-    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.5, 0.9, 1.2])
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[0.25, 0.5, 0.75, 0.9, 1.0, 1.2])
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.batch_log2 is not None:
