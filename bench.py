@@ -47,7 +47,13 @@ WORKLOADS = {
                                        batch_log2=20, slices=4, weights="lognormal3"),
     "rmat22_ppr_maxdeg": dict(scale=22, algo="ppr", p=1.0, q=1.0, mode="fast", L=100, types=None,
                               batch_log2=20, slices=1, starts="maxdeg"),
+    # small case of the headline kernel for ncu captures with DRAM counters
+    # (graph 4.3 GB, 2^18 queries per launch)
+    "rmat24_node2vec": dict(scale=24, algo="node2vec", p=1.0, q=2.0, mode="fast", L=80, types=None,
+                            batch_log2=18, slices=64),
 }
+
+NOMINAL_HBM_GBS = 8000.0  # the HBM figure the hot-path target is stated against
 
 
 def describe(w):
@@ -171,22 +177,25 @@ def slice_starts(n, k, slices, batch, device, w=None, g=None):
 
 
 def cpu_oracle_sample(g_host, w, seconds=15.0, threads=None, seed=42):
-    """The CPU oracle (as it stands: exact-mode walker, one query per call
-    range) on a bounded sample of the workload's queries, on `threads` host
-    threads over disjoint query ranges.  Returns (steps/s, threads, description)."""
+    """The CPU oracle (as it stands: the exact-mode C walker) on a bounded
+    sample of the workload's queries, on `threads` host threads over disjoint
+    query ranges.  The sample's starts are drawn uniformly over the whole
+    vertex range by hash, so the oracle sees the same mix of hub and leaf
+    starts as one query per vertex.  Returns (steps/s, threads, description)."""
     import numpy as np
+
+    import fw_inputs as fi
     import oracle
     oracle.build()
     csr = oracle.CSR(g_host)
     prm = oracle.Params(p=w["p"], q=w["q"], scale=2)
     threads = threads or os.cpu_count() or 1
     n = g_host.n
-    # sample: queries spread over the whole vertex range (vertex ids 0, s, 2s, ...)
     per_call = 8
     total_steps = 0
     calls = 0
     t0 = time.time()
-    stride = max(1, n // 100003)
+    pool = fi.random_starts(n, 1 << 20, 4243 + seed).numpy()
 
     hub = None
     if w.get("starts") == "maxdeg":
@@ -196,7 +205,7 @@ def cpu_oracle_sample(g_host, w, seconds=15.0, threads=None, seed=42):
         if hub is not None:
             st = np.full(per_call, hub, dtype=np.int32)
         else:
-            st = np.arange(ci * per_call * stride, (ci + 1) * per_call * stride, stride, dtype=np.int32) % n
+            st = pool[(ci * per_call) % pool.size:][:per_call]
         _, plen = oracle.walk_exact(csr, w["algo"], prm, st, w["L"], seed, q0=ci * per_call)
         return int((plen - 1).sum())
 
@@ -216,9 +225,11 @@ def cpu_oracle_sample(g_host, w, seconds=15.0, threads=None, seed=42):
             total_steps += f.result()
             calls += 1
     dt = time.time() - t0
-    where = "every start at the max-degree vertex" if hub is not None else "starts spread over the vertex range"
-    desc = (f"oracle (exact-mode C walker) on {calls * per_call} queries of the same workload "
-            f"({where}), {threads} threads, {dt:.1f} s")
+    where = ("every start at the max-degree vertex" if hub is not None
+             else "starts uniform over the whole vertex range by hash")
+    desc = (f"oracle (exact-mode C walker, integer weights) on {calls * per_call} queries of the same graph, "
+            f"algorithm and length ({where}), {threads} threads, {dt:.1f} s; the GPU line walks in "
+            f"{w['mode']} mode")
     return total_steps / dt, threads, desc
 
 
@@ -257,10 +268,11 @@ def _dist_env():
     return env_rank()[0], env_rank()[1], env_rank()[2]
 
 
-def run_serve(args):
-    """Served form (config 5): Poisson arrivals at swept rates on a resident
-    R-MAT graph; steps/s and p50/p99 latency beside the plain batch of the
-    same request mix."""
+def serve_block(args):
+    """Served form (config 5): Poisson arrivals at swept offered loads on a
+    resident R-MAT graph; per load the served steps/s, p50/p99 latency
+    (submission to results in the caller's host buffers) and the clocks seen,
+    beside the plain batch of the same request mix."""
     import numpy as np
     import torch
 
@@ -284,8 +296,10 @@ def run_serve(args):
         reqs.append(dict(algo=a, starts=fi.random_starts(g.n, n_q, 1000 + i), max_len=L, seed=(i * 2654435761) & 0xFFFFFFFF,
                          p=2.0, q=0.5, ppr_stop=0.2))
     total_q = sum(r["starts"].numel() for r in reqs)
-    # plain batch of the same mix: one engine launch per request, back to back,
-    # and one launch for everything of each algorithm (upper bound)
+
+    # plain batch of the same mix: all requests of one algorithm merged into
+    # one launch, the three launches back to back (an upper bound for any
+    # batch server: no request boundaries, no admission, no copies out)
     def batch_once():
         outs = []
         for a in algos:
@@ -299,9 +313,12 @@ def run_serve(args):
         torch.cuda.synchronize()
         return sum(int((pl - 1).sum()) for _, pl in outs)
     batch_once()
+    clocks = ClockSampler(0)
+    clocks.start()
     t0 = time.perf_counter()
     steps_b = batch_once()
     tb = time.perf_counter() - t0
+    batch_clk = clocks.stop()
     batch_rate = steps_b / tb
     req_rate_cap = n_req / tb
     lines = []
@@ -309,6 +326,8 @@ def run_serve(args):
         srv = Server(dg, mode="fast", mem_budget=args.serve_mem_mb << 20, idle_ms=5.0)
         lam = frac * req_rate_cap
         gaps = rng.exponential(1.0 / lam, size=n_req)
+        clocks = ClockSampler(0)
+        clocks.start()
         t_start = time.perf_counter()
         at = t_start
         tickets = []
@@ -324,23 +343,36 @@ def run_serve(args):
             lat.append(l)
             steps += int((plen - 1).sum())
         t_end = time.perf_counter()
+        clk = clocks.stop()
         st = srv.stats()
         srv.close()
         lat = np.array(lat)
         lines.append({"offered_load": frac, "served_steps_per_s": steps / (t_end - t_start),
+                      "served_over_batch": steps / (t_end - t_start) / batch_rate,
                       "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                      "engine_launches": st["launches"]})
+                      "engine_launches": st["launches"], "clocks": clk})
     best = max(lines, key=lambda d: d["served_steps_per_s"])
-    out = {
-        "metric": "served walk steps/s", "value": best["served_steps_per_s"], "unit": "steps/s", "n_gpus": 1,
-        "higher_is_better": True, "data": "synthetic", "dtype": "f32",
-        "config": {"workload": f"served mix on R-MAT scale {scale}: {n_req} requests, sizes log-uniform [1, 65536] "
-                               f"({total_q} queries), algo uniform {{weighted, node2vec p=2 q=0.5, PPR 0.2}}, "
-                               f"length uniform [10, 80] (PPR cap 100), Poisson arrivals",
-                   "arena_mb": args.serve_mem_mb},
-        "plain_batch_steps_per_s": batch_rate, "served_over_batch": best["served_steps_per_s"] / batch_rate,
+    dg.free()
+    del g
+    torch.cuda.empty_cache()
+    return {
+        "metric": "served walk steps/s", "value": best["served_steps_per_s"], "unit": "steps/s",
+        "workload": f"served mix on R-MAT scale {scale}: {n_req} requests, sizes log-uniform [1, 65536] "
+                    f"({total_q} queries), algo uniform {{weighted, node2vec p=2 q=0.5, PPR 0.2}}, "
+                    f"length uniform [10, 80] (PPR cap 100), Poisson arrivals, fast mode, host outputs",
+        "arena_mb": args.serve_mem_mb,
+        "plain_batch_steps_per_s": batch_rate, "plain_batch_clocks": batch_clk,
+        "plain_batch": "the same requests merged per algorithm into 3 device launches back to back "
+                       "(device outputs): an upper bound for a batch server",
+        "served_over_batch": best["served_steps_per_s"] / batch_rate,
+        "best_offered_load": best["offered_load"],
         "sweep": lines,
     }
+
+
+def run_serve(args):
+    out = serve_block(args)
+    out.update({"n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "f32"})
     print(json.dumps(out), flush=True)
 
 
@@ -366,6 +398,8 @@ def run_sweep(args):
     stream = torch.cuda.current_stream(dev)
     points = [(10 ** e, 80) for e in range(2, 8)] + [(10 ** 6, L) for L in (10, 20, 40)]
     rows = []
+    clocks = ClockSampler(0)
+    clocks.start()
     for nq, L in points:
         starts = fi.random_starts(g.n, nq, 4242).to(dev)
         paths = torch.empty((nq, L + 1), dtype=torch.int32, device=dev)
@@ -383,7 +417,9 @@ def run_sweep(args):
         rows.append({"queries": nq, "length": L, "edges_per_s": st["rows_scanned"] / s,
                      "steps_per_s": st["steps"] / s, "ms": s * 1e3})
         del paths, plen
+    clk = clocks.stop()
     out = {"metric": "edges/s (scanned CSR entries per second)", "unit": "edges/s", "higher_is_better": True,
+           "clocks": clk,
            "n_gpus": 1, "dtype": "f32", "data": "synthetic",
            "config": {"workload": f"{algo} p={p:g} q={q:g}, fast mode, R-MAT scale {scale} "
                                   f"(a,b,c=.57,.19,.19, ef 16, symmetrised), random starts",
@@ -419,6 +455,8 @@ def run_batched(args):
     kw = dict(mode="fast", p=1.0, q=2.0)
     dg.walk_batched("node2vec", starts[:4096], L, 1, budget_bytes=budget, **kw)  # warm-up
     dg.stats_reset()
+    clocks = ClockSampler(0)
+    clocks.start()
     t0 = time.perf_counter()
     _, _, bq = dg.walk_batched("node2vec", starts, L, 2, budget_bytes=budget, paths=hp, path_len=hl, **kw)
     t_b = time.perf_counter() - t0
@@ -434,9 +472,10 @@ def run_batched(args):
     hl.copy_(dl)
     torch.cuda.synchronize(dev)
     t_1 = time.perf_counter() - t0
+    clk = clocks.stop()
     steps_1 = dg.stats()["steps"]
     out = {"metric": "walk steps/s, host outputs", "unit": "steps/s", "higher_is_better": True, "n_gpus": 1,
-           "dtype": "f32", "data": "synthetic",
+           "dtype": "f32", "data": "synthetic", "clocks": clk,
            "config": {"workload": f"node2vec p=1 q=2, fast mode, R-MAT scale {scale}, L={L}, {nq} random starts, "
                                   f"host (pinned) outputs of {nq * (L + 1) * 4 / 1e9:.2f} GB",
                       "budget_bytes": budget, "queries_per_batch": bq, "batches": (nq + bq - 1) // bq},
@@ -462,6 +501,8 @@ def run_samplers(args):
 
     torch.cuda.set_device(0)
     rows = []
+    clocks = ClockSampler(0)
+    clocks.start()
     for e in range(0, 21):
         n = 1 << e
         k = torch.arange(n, dtype=torch.int64)
@@ -476,12 +517,49 @@ def run_samplers(args):
                 res[m] = {"draws_per_s": reps / (ms / 1e3), "elements_per_s": reps * n / (ms / 1e3), "ms": ms}
             best = max(res, key=lambda m: res[m]["draws_per_s"])
             rows.append({"n": n, "width": width, "reps": reps, "best": best, **{m: res[m] for m in res}})
+    clk = clocks.stop()
     out = {"metric": "weighted draws per second", "unit": "draws/s", "higher_is_better": True, "n_gpus": 1,
-           "dtype": "f32", "data": "synthetic",
+           "dtype": "f32", "data": "synthetic", "clocks": clk,
            "config": {"workload": "one weight array of n entries ([1,5) on a 2^-14 grid), independent draws, "
                                   "samplers: expj (engine), dprs (Alg. 3), zprs (Alg. 4)"},
            "sweep": rows}
     print(json.dumps(out), flush=True)
+
+
+def full_config_block(dg, g, w, dev, stream, peak):
+    """The configuration as stated, in one launch: every query of the
+    workload (one per vertex) walked by a single engine launch, timed with
+    CUDA events on the launching stream, with its own clock samples."""
+    import torch
+    n_q = g.n
+    L = w["L"]
+    starts = torch.arange(n_q, dtype=torch.int32, device=dev)
+    paths = torch.empty((n_q, L + 1), dtype=torch.int32, device=dev)
+    plen = torch.empty(n_q, dtype=torch.int32, device=dev)
+    kw = dict(mode=w["mode"], p=w["p"], q=w["q"], scale=2)
+    torch.cuda.synchronize(dev)
+    dg.stats_reset(stream)
+    clocks = ClockSampler(dev.index or 0)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    dg.walk(w["algo"], starts, L, 42, paths=paths, path_len=plen, stream=stream, **kw)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    st = dg.stats()
+    achieved = st["algo_bytes"] / (ms / 1e3) / 1e9
+    out = {"queries": n_q, "launches": 1, "ms": ms, "steps": st["steps"],
+           "steps_per_s": st["steps"] / (ms / 1e3), "walks": st["walks"],
+           "output_bytes": paths.numel() * 4 + plen.numel() * 4,
+           "roofline": {"achieved": achieved, "peak": peak, "frac": achieved / peak,
+                        "frac_vs_8tbs": achieved / NOMINAL_HBM_GBS, "algo_bytes": st["algo_bytes"]},
+           "clocks": clk}
+    del paths, plen, starts
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -494,7 +572,10 @@ def main():
     ap.add_argument("--batch-log2", type=int, default=None)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="launches timed end to end (host buffers)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-full", action="store_true", help="skip the one-launch run of every query of the workload")
+    ap.add_argument("--no-served", action="store_true", help="skip the served-form block")
     ap.add_argument("--threads", type=int, default=0, help="CTA size (0 = library default)")
     ap.add_argument("--slots", type=int, default=0, help="walk slots per CTA (0 = default)")
     ap.add_argument("--d-t", type=int, default=0, help="hub threshold d_t (0 = default)")
@@ -606,9 +687,10 @@ def main():
         torch.cuda.synchronize(dev)
         if world > 1:
             dist.barrier()
+        e2e_k = max(1, min(args.steps, args.e2e_steps))
         t0 = time.perf_counter()
         h2d = d2h = 0
-        for i in range(args.steps):
+        for i in range(e2e_k):
             k = args.warmup + i
             n_q = hs[k].numel()
             dg.walk(w["algo"], hs[k], w["L"], 42, q_id0=starts[k][1], paths=hp[:n_q], path_len=hl[:n_q],
@@ -618,8 +700,10 @@ def main():
         t1 = time.perf_counter()
         e2e_steps = reduce_scalar(dg.stats()["steps"], "sum", dev)
         e2e_s = reduce_scalar(t1 - t0, "max", dev)
-        e2e = {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d // args.steps,
-               "d2h_bytes_per_step": d2h // args.steps}
+        e2e = {"value": e2e_steps / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": h2d // e2e_k,
+               "d2h_bytes_per_step": d2h // e2e_k, "launches": e2e_k,
+               "how": "fw_walk_ex with pinned host starts, paths and path_len (the library stages them); "
+                      "wall clock around the launches, copies included"}
 
     peak, peak_kind = load_peaks()
     algo_bytes_per_launch = st["algo_bytes"] / args.steps
@@ -636,6 +720,7 @@ def main():
                    "graph_gen_s": round(gen_s, 1), "tuning": dg.get_tuning()},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
+                     "frac_vs_8tbs": achieved / NOMINAL_HBM_GBS,
                      "traffic": prof[0] * algo_bytes_per_launch if prof else None,
                      "traffic_source": (f"{prof[1]}: ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
                                         f"full-size launch per algorithmic byte ({prof[0]}), times this run's "
@@ -649,14 +734,21 @@ def main():
         "e2e": e2e,
         "counters": {k: st[k] for k in ("steps", "rows_scanned", "warp_steps", "block_steps", "n2v_tests")},
     }
+    del paths, plen
+    if not args.no_full and world == 1 and w.get("starts") != "maxdeg":
+        line["full_config"] = full_config_block(dg, g, w, dev, stream, peak)
     if g_host is not None:
         del g
         torch.cuda.empty_cache()
         v, cores, desc = cpu_oracle_sample(g_host, w, seconds=args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": cores, "kind": "oracle", "sample": desc}
+    dg.free()
+    if not args.no_served and world == 1:
+        del g_host
+        torch.cuda.empty_cache()
+        line["served"] = serve_block(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    dg.free()
     if world > 1:
         dist.destroy_process_group()
 

@@ -57,7 +57,12 @@ typedef enum {
                       Philox-4x32-10 block per (seed, query, step) and an exact
                       inverse-transform pick: bit-identical to the CPU oracle */
     FW_FAST = 1    /* FP32 weights (w_f32); single-pass weighted reservoir
-                      sampling (exponential race with exponential jumps) */
+                      sampling (exponential race with exponential jumps).  A
+                      row is cut into segments of 16384 entries (counted from
+                      its first 16-entry-aligned group; more per segment past
+                      64 segments), segment j draws from random stream j and
+                      the smallest race time wins, whichever sampler scans the
+                      row: fast-mode paths do not depend on fw_tuning */
 } fw_mode;
 
 /* fw_load_csr flags */
@@ -79,8 +84,11 @@ typedef struct fw_graph fw_graph;
  *   n2v_p, n2v_q    node2vec return (paper's a) and in-out (paper's b)
  *                   parameters of Eq. 2.  Fast mode uses the factors 1/p, 1,
  *                   1/q in FP32.  Exact mode uses the integers S/p, S, S/q
- *                   with S = n2v_scale (must all be positive integers, else
- *                   FW_EINVAL); p = 2, q = 0.5, S = 2 gives 1, 2, 4.
+ *                   with S = n2v_scale (must all be positive integers in
+ *                   [1, 65536], else FW_EINVAL); p = 2, q = 0.5, S = 2 gives
+ *                   1, 2, 4.  Exact mode multiplies weight by factor in 32
+ *                   bits, so max(w_u32) × the largest factor must stay below
+ *                   2^32, else the walk call returns FW_EINVAL.
  *   schema          MetaPath labels, schema[t mod schema_len] is required
  *                   at move t (0-based); schema_len in [1, 16].
  *   ppr_stop        PPR stop probability in [0, 1]; the walk stops after a
@@ -106,7 +114,9 @@ typedef struct {
  *                   by one warp, larger rows by the whole CTA (default 16384;
  *                   exact mode caps it at 8184).
  *   ctas_per_sm     persistent CTAs per SM (0 = as many as fit).
- * Zero fields mean "default".
+ * Zero fields mean "default".  No field changes a walk's result: exact mode is
+ * bit-identical to the CPU oracle under every tuning, and fast mode draws each
+ * row with the same segment streams whichever sampler takes it.
  */
 typedef struct {
     int32_t block_threads;
@@ -212,17 +222,24 @@ int fw_walk_multi(fw_graph* g, const fw_request* reqs, int32_t n_req, void* stre
  *
  *   g, reqs, n_req, stream   as fw_walk_multi; every buffer is device memory
  *                            the caller owns; 1 <= n_req <= FW_NOALLOC_MAX_REQS.
- * Scratch: the request table, the query cursor and the counters of the launch
- * live in one static device array compiled into the library (about
- * FW_NOALLOC_MAX_REQS × 168 bytes + 128 bytes), which every GPU that loads the
- * library holds until the process exits.  Nothing is allocated: no cudaMalloc,
- * no cudaFree, no host heap.  The first call on a device looks the array's
- * device address up (cudaGetSymbolAddress) with that device current: make that
- * first call before any stream capture.  The array is shared by all calls and
- * keeps the last call's contents; each call resets the cursor and counters it
- * uses.  Two calls whose launches overlap on the GPU (different streams, no
- * ordering between them) race on the array: order them on one stream.  Counts
- * of these launches do not appear in fw_stats.
+ * Scratch: the request table and the query cursor of the launch live in one
+ * static device array compiled into the library (about FW_NOALLOC_MAX_REQS ×
+ * 168 bytes + 128 bytes), which every GPU that loads the library holds until
+ * the process exits.  Nothing is allocated: no cudaMalloc, no cudaFree, no
+ * host heap.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current: make that first call
+ * before any stream capture.  The array is shared by all calls and keeps the
+ * last call's contents; each call resets the cursor it uses.  Two calls whose
+ * launches overlap on the GPU (different streams, no ordering between them)
+ * race on the array: order them on one stream.
+ * The request table is copied from pageable host memory, and such a copy
+ * waits for the work already queued on `stream`: the call returns only after
+ * the stream's earlier work has finished (the walk itself is then queued and
+ * runs asynchronously).
+ * The launch adds its counts to the graph's counters, which the graph holds
+ * from fw_load_csr on: fw_stats reports them like those of fw_walk, and
+ * returns FW_EINVAL when a start or prev was out of range (written as an
+ * empty path) and FW_ETIMEOUT when a bounded device wait ran out.
  * Errors: FW_EINVAL (n_req outside [1, FW_NOALLOC_MAX_REQS], host buffers,
  * bad parameters), FW_ECUDA.
  */
@@ -245,9 +262,10 @@ int fw_walk_noalloc(fw_graph* g, const fw_request* reqs, int32_t n_req, void* st
  *   paths equal one launch over all queries.
  *   batch_q (may be NULL) receives |P_G| as used (at most n_q).
  * Synchronous; the work is added to the graph's counters (fw_stats).
- * Errors: FW_EINVAL (arguments, parameters), FW_ENOMEM (the budget does not
- * hold one query in each pool, or an allocation failed), FW_ECUDA,
- * FW_ETIMEOUT (a device wait gave up).
+ * Errors: FW_EINVAL (arguments, parameters; or, after the run, starts out of
+ * range, whose paths are written empty), FW_ENOMEM (the budget does not hold
+ * one query in each pool, or an allocation failed), FW_ECUDA, FW_ETIMEOUT (a
+ * device wait gave up).
  */
 int fw_walk_batched(fw_graph* g, int32_t algo, const fw_params* p, const int32_t* h_starts, int64_t n_q,
                     const int32_t* h_lengths, int32_t max_len, uint64_t seed, int64_t q_id0,
@@ -295,8 +313,11 @@ int fw_walk_ex(fw_graph* g, int32_t algo, const fw_params* p, const int32_t* sta
  *   idle_ms      the engine returns after this long without work and is
  *                relaunched when work arrives (<= 0: 20 ms).
  * A request's random counters use its own seed and its own query ids
- * (q_id0 + i), so its paths equal those of the same request run alone
- * (bit for bit in exact mode; in fast mode for the same engine tuning).
+ * (q_id0 + i), so its paths equal those of the same request run alone, bit
+ * for bit in both modes (no engine tuning changes a result).
+ * The engine's warps also return by themselves after 2 s without work (a
+ * bounded device wait); the server then relaunches the engine for the next
+ * request.
  * Latency = submission to outputs in the caller's buffers.
  * Errors: FW_EINVAL (arguments, mode mismatch, start out of range), FW_EBUSY
  * (a request larger than the whole arena), FW_ETIMEOUT (wait), FW_ENOMEM,

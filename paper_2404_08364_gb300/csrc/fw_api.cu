@@ -606,14 +606,16 @@ extern "C" int fw_philox(const uint32_t* in, uint32_t* out, int64_t n, void* str
 // ------------------------------------------------------ no-allocation launch
 //
 // For callers that cannot allocate device memory when they walk: the request
-// table, query cursor and counters of the launch live in this one file-scope
-// device array instead of graph-owned or freshly allocated memory.  Host code
-// may not pass the symbol itself to a kernel (in host code it names a host
-// stand-in), so its device address is looked up once per device.
+// table and query cursor of the launch live in this one file-scope device
+// array instead of freshly allocated memory.  The launch's counts go to the
+// graph's own counters (allocated when the graph was loaded), so fw_stats
+// reports them, bad starts and timed-out waits included.  Host code may not
+// pass the symbol itself to a kernel (in host code it names a host stand-in),
+// so its device address is looked up once per device.
 
 namespace {
 struct NoAllocScratch {
-    Scratch s;                          // cursor + counters (reset every call)
+    Scratch s;                          // s.cursor: reset every call (s.counters unused)
     ReqDev reqs[FW_NOALLOC_MAX_REQS];   // the launch's request table
 };
 }  // namespace
@@ -676,15 +678,23 @@ extern "C" int fw_walk_noalloc(fw_graph* G, const fw_request* reqs, int32_t n_re
     }
     if (total == 0) return FW_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    // the table comes from pageable host memory: the copy has taken the data
-    // by the time cudaMemcpyAsync returns, so the staging array may be reused
+    // The table comes from pageable host memory.  Such a copy waits for the
+    // work already queued on the stream and has taken the data by the time
+    // cudaMemcpyAsync returns, so the staging array may be reused at once.
     FW_CUDA_TRY(cudaMemcpyAsync(dev->reqs, g_noalloc_host, sizeof(ReqDev) * (size_t)n_req,
                                 cudaMemcpyHostToDevice, st));
-    FW_CUDA_TRY(cudaMemsetAsync(&dev->s, 0, sizeof(Scratch), st));  // the cursor must start at zero
+    FW_CUDA_TRY(cudaMemsetAsync(&dev->s.cursor, 0, sizeof(unsigned long long), st));  // starts at zero
     ReqTable tab;
     memset(&tab, 0, sizeof tab);
     tab.ext = dev->reqs;
-    cudaError_t e = launch_walk(G->g, mode, tab, n_req, total, &dev->s, G->tuning, st);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    const bool timed = cap == cudaStreamCaptureStatusNone;
+    if (timed) FW_CUDA_TRY(cudaEventRecord(G->ev0, st));
+    cudaError_t e = launch_walk(G->g, mode, tab, n_req, total, &dev->s.cursor, G->scratch->counters, G->tuning, st);
     if (e != cudaSuccess) return fail(FW_ECUDA, "fw_walk_noalloc: launch: %s", cudaGetErrorString(e));
+    if (timed) FW_CUDA_TRY(cudaEventRecord(G->ev1, st));
+    G->timed = timed;
+    G->last_stream = st;
     return FW_OK;
 }

@@ -169,5 +169,8 @@ extern "C" int fw_walk_batched(fw_graph* g, int32_t algo, const fw_params* p, co
         return fail_b(e == cudaErrorMemoryAllocation ? FW_ENOMEM : FW_ECUDA, "fw_walk_batched: %s",
                       cudaGetErrorString(e));
     if (cnt[C_TIMEOUT]) return fail_b(FW_ETIMEOUT, "fw_walk_batched: a device wait timed out");
+    if (cnt[C_BAD_INPUT])
+        return fail_b(FW_EINVAL, "fw_walk_batched: %llu queries had an out-of-range start (written as empty paths)",
+                      (unsigned long long)cnt[C_BAD_INPUT]);
     return FW_OK;
 }

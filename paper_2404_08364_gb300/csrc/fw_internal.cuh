@@ -154,9 +154,17 @@ struct Tuning {
 };
 
 // Launch the persistent walk engine over `n_req` requests (device array
-// `reqs`) holding `total` queries.  Defined in fw_walk.cu.
+// `reqs`) holding `total` queries; the warps claim queries from `cursor`
+// (which must be 0 when the launch starts) and add their counts to
+// `counters` (C_NUM words).  Defined in fw_walk.cu.
 cudaError_t launch_walk(const GraphDev& g, int mode, const ReqTable& reqs, int n_req, int64_t total,
-                        Scratch* scratch, const Tuning& tune, cudaStream_t stream);
+                        unsigned long long* cursor, unsigned long long* counters, const Tuning& tune,
+                        cudaStream_t stream);
+
+inline cudaError_t launch_walk(const GraphDev& g, int mode, const ReqTable& reqs, int n_req, int64_t total,
+                               Scratch* scratch, const Tuning& tune, cudaStream_t stream) {
+    return launch_walk(g, mode, reqs, n_req, total, &scratch->cursor, scratch->counters, tune, stream);
+}
 
 // Launch the engine in served mode (runs until stopped or idle).  Defined in
 // fw_walk.cu.

@@ -50,6 +50,13 @@ constexpr int WIN = 128;          // staged window of N(prev) per warp (node2vec
 constexpr int SW_MAX = 8;         // walk slots per warp, upper bound
 constexpr int NHUB = 4;           // hub tasks open at once per CTA
 constexpr int NSEG_MAX = 64;      // segments per hub task
+// A row is cut into segments of kSegQuads quads (16384 entries, counted from
+// its first aligned 16-entry group), or more for rows past NSEG_MAX such
+// segments.  In fast mode segment j draws from random stream j and the step
+// takes the smallest race time over the segments, whichever sampler (a warp
+// alone, or a CTA hub task) scans the row: the pick depends on the row, not
+// on the threshold d_t or the launch shape.
+constexpr int kSegQuads = 4096;
 constexpr int NCHUNK_MAX = 64;    // exact warp sampler: chunk sums (d_t <= 8192)
 constexpr int NST = 3;            // TMA ring stages per warp
 constexpr int CHQ = 32;           // quads per chunk (one per lane)
@@ -595,6 +602,20 @@ struct WarpRes {
     }
 };
 
+// The order in which segment results compete: the smaller race time wins,
+// the smaller row index breaks a tie (race times are positive, so their FP32
+// bit patterns order as the values do).
+__device__ __forceinline__ unsigned long long race_key(const WarpRes& r) {
+    return ((unsigned long long)__float_as_uint(r.tau) << 32) | (unsigned)r.sel;
+}
+
+// Quads per segment for a row range of nq quads: seg_q, or more for rows of
+// more than NSEG_MAX such segments; a multiple of 32 (one quad per lane).
+__device__ __forceinline__ long long seg_quads(long long nq, int seg_q) {
+    const long long sq = max((long long)seg_q, (nq + NSEG_MAX - 1) / NSEG_MAX);
+    return (sq + 31) & ~31ll;
+}
+
 // A new record at row entry idx of weight w (uniform across the warp).
 __device__ __noinline__ WarpRes warp_record(WarpRes r, int idx, float w, uint64_t seed, uint64_t qid, uint32_t t,
                                             uint32_t stream) {
@@ -1042,8 +1063,7 @@ template <int MODE, int NT>
 __device__ __forceinline__ void hub_merge(const GraphDev& g, Smem<NT>& sm, HubTask& H, int j, const WarpRes& res,
                                           unsigned long long lane_sum, int lane, int* win, Counters& cnt) {
     if (MODE == MODE_FAST) {
-        if (lane == 0 && res.sel >= 0)
-            atomicMin(&H.best, ((unsigned long long)__float_as_uint(res.tau) << 32) | (unsigned)res.sel);
+        if (lane == 0 && res.sel >= 0) atomicMin(&H.best, race_key(res));
     } else {
         const unsigned long long s = warp_sum_u64(lane_sum);
         if (lane == 0) H.seg_sum[j] = s;
@@ -1080,7 +1100,8 @@ constexpr int min_ctas(int nt) { return nt >= 512 ? 1 : (nt >= 256 ? 3 : 5); }
 
 template <int MODE, int NT>
 __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, const __grid_constant__ ReqTable tab, int n_req,
-                                                  long long total, Scratch* scratch, int sw, int d_t, int seg_q,
+                                                  long long total, unsigned long long* cursor,
+                                                  unsigned long long* counters, int sw, int d_t, int seg_q,
                                                   ServeDev sv) {
     const bool serving = sv.ring != nullptr;
     const ReqDev* __restrict__ reqs = serving ? sv.ring : (tab.ext ? tab.ext : tab.r);
@@ -1172,7 +1193,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                         if (qi < 0) continue;  // nothing published right now: the slot stays empty
                     } else {
                         long long gq = 0;
-                        if (lane == 0) gq = (long long)atomicAdd(&scratch->cursor, 1ull);
+                        if (lane == 0) gq = (long long)atomicAdd(cursor, 1ull);
                         gq = __shfl_sync(FULL, gq, 0);
                         if (gq >= total) {
                             exhausted = true;
@@ -1204,7 +1225,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                         sm.req[jj] = r;
                         sm.k[jj] = 0;
                         if (start < 0 || start >= g.n || pv < -1 || pv >= g.n || t0 < 0) {
-                            atomicAdd(&scratch->counters[C_BAD_INPUT], 1ull);
+                            atomicAdd(&counters[C_BAD_INPUT], 1ull);
                             st = ST_FINISH;  // written out as an empty path
                         } else {
                             Rq.paths[qi * ((long long)Rq.max_len + 1)] = start;
@@ -1284,7 +1305,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                     idle_since = global_timer_ns();
                 } else if (__shfl_sync(FULL, (int)(global_timer_ns() - idle_since > kWaitLimitNs), 0)) {
                     if (lane == 0) {
-                        atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
+                        atomicAdd(&counters[C_TIMEOUT], 1ull);
                         sm.abort_flag = 1;
                     }
                     break;
@@ -1338,8 +1359,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
                     if (hh >= 0) {
                         HubTask& H = sm.hub[hh];
                         const long long nq = qb - qa;
-                        long long sq = max((long long)seg_q, (nq + NSEG_MAX - 1) / NSEG_MAX);
-                        sq = (sq + 31) & ~31ll;
+                        const long long sq = seg_quads(nq, seg_q);
                         H.slot = s;
                         H.seg_q = (int)sq;
                         H.nseg = (int)((nq + sq - 1) / sq);
@@ -1371,12 +1391,28 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
         nap = 128;
 
         // ------------------------------------ stream the row range (one site)
+        // A hub segment or an exact-mode row is one range.  A fast-mode row
+        // sampled by this warp alone is cut into the hub path's segments,
+        // segment j drawing from random stream j, and the step keeps the
+        // smallest (race time, index) over them, as a hub task's merge does.
         WarpRes res;
-        res.init();
         unsigned long long lane_sum = 0;
+        unsigned long long best = ~0ull;
         const long long end = c.beg + c.d;
-        if (!scan_range<MODE>(g, c, qa, qb, end, lane, win, P, res, lane_sum, sums, stream, seed, qid, t)) {
-            if (lane == 0) atomicAdd(&scratch->counters[C_TIMEOUT], 1ull);
+        const long long sq = (MODE == MODE_FAST && !seg) ? seg_quads(qb - qa, seg_q) : qb - qa;
+        bool scanned = true;
+        for (long long sa = qa; sa < qb; sa += sq) {
+            res.init();
+            if (!scan_range<MODE>(g, c, sa, min(qb, sa + sq), end, lane, win, P, res, lane_sum, sums, stream, seed,
+                                  qid, t)) {
+                scanned = false;
+                break;
+            }
+            if (res.sel >= 0) best = min(best, race_key(res));
+            ++stream;
+        }
+        if (!scanned) {
+            if (lane == 0) atomicAdd(&counters[C_TIMEOUT], 1ull);
             break;
         }
 
@@ -1388,7 +1424,7 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
         int sel = -1;
         uint32_t oz = 0xFFFFFFFFu;
         if (MODE == MODE_FAST) {
-            sel = res.sel;
+            sel = best == ~0ull ? -1 : (int)(best & 0xFFFFFFFFull);
             if (sel >= 0 && R->algo == FW_PPR) oz = step_block(seed, qid, t).z;
         } else {
             const unsigned long long W = warp_sum_u64(lane_sum);
@@ -1418,12 +1454,13 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
     }
     if (lane == 0)
         for (int i = 0; i < C_NUM; ++i)
-            if (cnt.v[i]) atomicAdd(&scratch->counters[i], cnt.v[i]);
+            if (cnt.v[i]) atomicAdd(&counters[i], cnt.v[i]);
 }
 
 template <int MODE, int NT>
-cudaError_t launch_one(const GraphDev& g, const ReqTable& reqs, int n_req, int64_t total, Scratch* scratch,
-                       const Tuning& tu, cudaStream_t stream) {
+cudaError_t launch_one(const GraphDev& g, const ReqTable& reqs, int n_req, int64_t total,
+                       unsigned long long* cursor, unsigned long long* counters, const Tuning& tu,
+                       cudaStream_t stream) {
     auto kern = walk_kernel<MODE, NT>;
     const size_t dyn = (size_t)(NT / 32) * WarpSmem<MODE>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -1443,7 +1480,8 @@ cudaError_t launch_one(const GraphDev& g, const ReqTable& reqs, int n_req, int64
     if (MODE == MODE_EXACT) d_t = min(d_t, NCHUNK_MAX * 128 - 8);  // at most NCHUNK_MAX chunks
     ServeDev none;
     memset(&none, 0, sizeof none);
-    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, reqs, n_req, (long long)total, scratch, sw, d_t, 4096, none);
+    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, reqs, n_req, (long long)total, cursor, counters, sw, d_t,
+                                              kSegQuads, none);
     return cudaGetLastError();
 }
 
@@ -1472,7 +1510,8 @@ cudaError_t launch_serve_one(const GraphDev& g, const ServeDev& sv, Scratch* scr
     if (MODE == MODE_EXACT) d_t = min(d_t, NCHUNK_MAX * 128 - 8);
     ReqTable tab;
     memset(&tab, 0, sizeof tab);
-    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, tab, 0, 0ll, scratch, sw, d_t, 4096, sv);
+    kern<<<(unsigned)grid, NT, dyn, stream>>>(g, tab, 0, 0ll, &scratch->cursor, scratch->counters, sw, d_t,
+                                              kSegQuads, sv);
     return cudaGetLastError();
 }
 
@@ -1510,20 +1549,21 @@ cudaError_t launch_serve(const GraphDev& g, int mode, const ServeDev& sv, Scratc
 }
 
 cudaError_t launch_walk(const GraphDev& g, int mode, const ReqTable& reqs, int n_req, int64_t total,
-                        Scratch* scratch, const Tuning& tune, cudaStream_t stream) {
+                        unsigned long long* cursor, unsigned long long* counters, const Tuning& tune,
+                        cudaStream_t stream) {
     const Tuning tu = sanitize_tuning(tune);
     if (total <= 0) return cudaSuccess;
     const bool exact = mode == FW_EXACT;
     switch (tu.block_threads) {
         case 128:
-            return exact ? launch_one<MODE_EXACT, 128>(g, reqs, n_req, total, scratch, tu, stream)
-                         : launch_one<MODE_FAST, 128>(g, reqs, n_req, total, scratch, tu, stream);
+            return exact ? launch_one<MODE_EXACT, 128>(g, reqs, n_req, total, cursor, counters, tu, stream)
+                         : launch_one<MODE_FAST, 128>(g, reqs, n_req, total, cursor, counters, tu, stream);
         case 512:
-            return exact ? launch_one<MODE_EXACT, 512>(g, reqs, n_req, total, scratch, tu, stream)
-                         : launch_one<MODE_FAST, 512>(g, reqs, n_req, total, scratch, tu, stream);
+            return exact ? launch_one<MODE_EXACT, 512>(g, reqs, n_req, total, cursor, counters, tu, stream)
+                         : launch_one<MODE_FAST, 512>(g, reqs, n_req, total, cursor, counters, tu, stream);
         default:
-            return exact ? launch_one<MODE_EXACT, 256>(g, reqs, n_req, total, scratch, tu, stream)
-                         : launch_one<MODE_FAST, 256>(g, reqs, n_req, total, scratch, tu, stream);
+            return exact ? launch_one<MODE_EXACT, 256>(g, reqs, n_req, total, cursor, counters, tu, stream)
+                         : launch_one<MODE_FAST, 256>(g, reqs, n_req, total, cursor, counters, tu, stream);
     }
 }
 

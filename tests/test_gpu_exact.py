@@ -198,3 +198,25 @@ def test_config3_rmat22_metapath_and_ppr_one_launch(orc):
     idx = np.random.default_rng(1).choice(g.n, 200, replace=False)
     _sampled(orc, g, "metapath", starts.cpu(), 80, 42, mp, ml, orc.Params(), idx)
     _sampled(orc, g, "ppr", starts.cpu(), 100, 42, pp, pl, orc.Params(ppr_stop=0.2), idx)
+
+
+@pytest.mark.slow
+def test_rmat22_ppr_from_max_degree_vertex_sampled(orc):
+    """The paper's PPR workload (Section 6.1): every query starts at the
+    max-degree vertex (stop 0.2, cap 100), so every walk's first step
+    competes for the CTAs' hub-task entries; 2^20 queries in one launch with
+    the default tuning, 200 of them recomputed by the oracle."""
+    g = cached_graph("rmat", 22, 2)
+    dg = device_graph(g)
+    deg = g.row_ptr[1:] - g.row_ptr[:-1]
+    hub = int(deg.argmax())
+    n_q = 1 << 20
+    starts = torch.full((n_q,), hub, dtype=torch.int32, device="cuda")
+    dg.stats_reset()
+    paths, plen = dg.walk("ppr", starts, 100, 42, mode="exact", ppr_stop=0.2)
+    st = dg.stats()
+    check_valid(g, paths, plen, "ppr")
+    assert st["block_steps"] >= n_q  # the first step of every walk is a hub row
+    paths, plen = paths.cpu(), plen.cpu()
+    idx = np.random.default_rng(5).choice(n_q, 200, replace=False)
+    _sampled(orc, g, "ppr", starts.cpu(), 100, 42, paths, plen, orc.Params(ppr_stop=0.2), idx)

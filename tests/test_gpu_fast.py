@@ -205,3 +205,57 @@ def test_validity_configs_fast():
     c2 = np.append(counts[keep], counts[~keep].sum())
     e2 = np.append(e[keep], e[~keep].sum())
     assert stats.chisquare(c2, e2).pvalue > P_MIN
+
+
+@pytest.fixture(scope="module")
+def g_lognormal():
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    # the recipe uses float64 exp/log/cos: generate once and give the same
+    # arrays to the GPU and to the oracle
+    return fi.rmat(18, weights="lognormal3", device=dev).to("cpu")
+
+
+def test_T6_lognormal_sigma3_weights(orc, g_lognormal):
+    """Log-normal weights with sigma = 3 (Appendix C.1) span about eight
+    decades, where an FP32 reservoir's running sums could drift: one step
+    of the weighted rule from a row of about 5000 entries, and of node2vec
+    (p=2, q=0.5) from the same row with a previous vertex that gives all
+    three classes."""
+    g = g_lognormal
+    dg = device_graph(g)
+    cur = _pick_vertex(g, 4000, 6000)
+    w = g.w_f32[int(g.row_ptr[cur]):int(g.row_ptr[cur + 1])].double()
+    assert float(w.max() / w.min()) > 1e6
+    nxt = _one_step(dg, "weighted", cur, -1, 0, 20241205)
+    tv, pv = _compare(g, nxt, _law(orc, g, "weighted", cur, -1, 0), cur, bins=64)
+    assert tv <= TV_MAX and pv > P_MIN, ("weighted", tv, pv)
+    prev = _pick_prev_with_mixed_classes(g, cur)
+    nxt = _one_step(dg, "node2vec", cur, prev, 4, 20241206, p=2.0, q=0.5)
+    p = _law(orc, g, "node2vec", cur, prev, 4, p=2.0, q=0.5)
+    tv, pv = _compare(g, nxt, p, cur, bins=64)
+    assert tv <= TV_MAX and pv > P_MIN, ("node2vec", tv, pv)
+
+
+def test_fast_paths_do_not_depend_on_tuning():
+    """Fast mode cuts every row into the same 16K-entry segments with one
+    random stream each, whether a warp or a CTA hub task samples it: the
+    paths are bit-identical under any d_t and launch shape."""
+    g = cached_graph("rmat", 20, 2)
+    dg = device_graph(g)
+    d = g.row_ptr[1:] - g.row_ptr[:-1]
+    assert int(d.max()) > 3 * 16384  # rows of several segments exist
+    starts = fi.random_starts(g.n, 20000, 17, "cuda")
+    starts[:64] = torch.argsort(d, descending=True)[:64].to(torch.int32).cuda()  # start on the hubs too
+    outs = []
+    for tu in (dict(), dict(d_warp=256), dict(d_warp=1 << 20), dict(block_threads=512, slots=64, d_warp=1024),
+               dict(block_threads=256, slots=8, d_warp=100000)):
+        dg.set_tuning(**tu)
+        res = []
+        for algo in ("weighted", "node2vec", "metapath"):
+            p, l = dg.walk(algo, starts, 20, 31, mode="fast", p=2.0, q=0.5)
+            res.append((p, l))
+        outs.append(res)
+    dg.set_tuning()
+    for res in outs[1:]:
+        for (p0, l0), (p1, l1) in zip(outs[0], res):
+            assert torch.equal(l0, l1) and torch.equal(p0, p1)

@@ -30,7 +30,7 @@ def _mix(g, n_req, seed0, rng):
 
 
 @pytest.mark.parametrize("mode", ["exact", "fast"])
-def test_alone_equals_in_the_mix(mode):
+def test_alone_equals_in_the_mix(orc, mode):
     from paper_2404_08364_gb300 import Server
     g = cached_graph("rmat", 14, 2)
     dg = device_graph(g)
@@ -40,12 +40,19 @@ def test_alone_equals_in_the_mix(mode):
     tickets = [srv.submit(**r) for r in reqs]
     outs = [srv.result(t) for t in tickets]
     srv.close()
+    csr = orc.CSR(g)
     for r, (paths, plen, lat) in zip(reqs, outs):
         alone_p, alone_l = dg.walk(r["algo"], r["starts"].cuda(), r["max_len"], r["seed"], mode=mode, p=2.0, q=0.5,
                                    lengths=None if r["lengths"] is None else r["lengths"].cuda())
         assert torch.equal(plen, alone_l.cpu()), r["algo"]
         assert torch.equal(paths, alone_p.cpu()), r["algo"]
         assert lat > 0
+        if mode == "exact":
+            # and both equal the oracle, element by element
+            ref_p, ref_l = orc.walk_exact(csr, r["algo"], orc.Params(p=2.0, q=0.5), r["starts"], r["max_len"],
+                                          r["seed"], lengths=r["lengths"])
+            assert np.array_equal(plen.numpy(), ref_l), r["algo"]
+            assert np.array_equal(paths.numpy(), ref_p), r["algo"]
 
 
 def test_requests_arriving_while_others_run():
@@ -107,3 +114,27 @@ def test_ring_slots_reused_many_times():
                                    q=0.5, lengths=None if r["lengths"] is None else r["lengths"].cuda())
         assert torch.equal(plen, alone_l.cpu()), r["algo"]
         assert torch.equal(paths, alone_p.cpu()), r["algo"]
+
+
+def test_engine_returns_on_its_own_idle_limit_and_is_relaunched(orc):
+    """The host's idle stop (idle_ms) is set above the engine's own 2-s
+    device-side idle limit, so the engine's warps return by themselves after
+    2 s without work (a bounded wait running out, with no fault); the next
+    request must still be served, by a relaunched engine, with the right
+    result."""
+    from paper_2404_08364_gb300 import Server
+    g = cached_graph("rmat", 12, 2)
+    dg = device_graph(g)
+    srv = Server(dg, mode="exact", mem_budget=8 << 20, idle_ms=60000.0)
+    s = fi.random_starts(g.n, 200, 3)
+    a = srv.result(srv.submit("node2vec", s, 20, 5, p=2.0, q=0.5))
+    launches0 = srv.stats()["launches"]
+    time.sleep(3.0)  # longer than the engine's 2 s device idle limit, far below idle_ms
+    b = srv.result(srv.submit("node2vec", s, 20, 5, p=2.0, q=0.5))
+    st = srv.stats()
+    srv.close()
+    assert launches0 == 1 and st["launches"] == 2
+    ref_p, ref_l = orc.walk_exact(orc.CSR(g), "node2vec", orc.Params(p=2.0, q=0.5), s, 20, 5)
+    for paths, plen, _ in (a, b):
+        assert np.array_equal(plen.numpy(), ref_l)
+        assert np.array_equal(paths.numpy(), ref_p)
