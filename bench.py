@@ -370,6 +370,23 @@ def serve_block(args):
     }
 
 
+def served_child(args, limit_s=600.0):
+    """The served block in a child process with a time limit, so that a
+    served run that stops making progress ends the child (and its CUDA
+    context) instead of the benchmark."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--serve", "--serve-scale", str(args.serve_scale),
+           "--serve-requests", str(args.serve_requests), "--serve-mem-mb", str(args.serve_mem_mb),
+           "--serve-rates", *[str(r) for r in args.serve_rates]]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=limit_s)
+    except subprocess.TimeoutExpired:
+        return {"error": f"served run exceeded {limit_s:.0f} s and was stopped"}
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"error": f"served run failed (rc {r.returncode}): {r.stderr.strip().splitlines()[-1:] }"}
+    return json.loads(lines[-1])
+
+
 def run_serve(args):
     out = serve_block(args)
     out.update({"n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "f32"})
@@ -570,6 +587,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat25_node2vec", choices=sorted(WORKLOADS))
     ap.add_argument("--batch-log2", type=int, default=None)
+    ap.add_argument("--algo", default=None, choices=["weighted", "node2vec", "metapath", "ppr"],
+                    help="walk rule instead of the workload's (same graph and queries)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5, help="launches timed end to end (host buffers)")
@@ -594,6 +613,10 @@ def main():
     w = dict(WORKLOADS[args.workload])
     if args.batch_log2 is not None:
         w["batch_log2"] = args.batch_log2
+    if args.algo is not None:
+        w["algo"] = args.algo
+        if args.algo == "metapath" and w["types"] is None:
+            w["types"] = 2
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -707,7 +730,7 @@ def main():
 
     peak, peak_kind = load_peaks()
     algo_bytes_per_launch = st["algo_bytes"] / args.steps
-    prof = profiled_traffic_ratio(args.workload)
+    prof = profiled_traffic_ratio(args.workload) if w["algo"] == WORKLOADS[args.workload]["algo"] else None
     achieved = algo_bytes_per_launch / (ms_total / args.steps / 1e3) / 1e9
     line = {
         "metric": "walk steps/s", "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
@@ -746,7 +769,7 @@ def main():
     if not args.no_served and world == 1:
         del g_host
         torch.cuda.empty_cache()
-        line["served"] = serve_block(args)
+        line["served"] = served_child(args)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

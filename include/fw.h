@@ -107,9 +107,9 @@ typedef struct {
 /*
  * Engine tuning (Section 5.1's |P_L| and d_t and the launch shape).
  *   block_threads   threads per CTA: 128, 256 or 512 (anything else: the
- *                   default, 128).
+ *                   default, 512).
  *   slots           walks resident per CTA: the local task pool P_L, at most
- *                   8 per warp (default 16).
+ *                   8 per warp (default 4 per warp).
  *   d_warp          degree threshold d_t: rows with d <= d_warp are sampled
  *                   by one warp, larger rows by the whole CTA (default 16384;
  *                   exact mode caps it at 8184).

@@ -13,7 +13,7 @@
 //
 // A request's walks use request-local query ids and the request's own seed,
 // so its paths are the same alone and in any mix (bit for bit in exact mode;
-// in fast mode for the same engine tuning).
+// in fast mode too: no engine tuning changes a result).
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -326,6 +326,13 @@ extern "C" int fw_server_create(fw_graph* graph, int32_t mode, uint64_t mem_budg
     fw_server* S = new fw_server();
     S->graph = graph;
     graph_device_view(graph, &S->g, &S->device, &S->tuning);
+    // The resident engine keeps one CTA slot free on every SM for other
+    // streams' kernels (launch_serve), which needs several resident CTAs per
+    // SM: it runs 128-thread CTAs, four walks per warp, whatever the graph's
+    // batch tuning (that tuning's d_t is kept; no tuning changes a result).
+    S->tuning.block_threads = 128;
+    S->tuning.slots = 16;
+    S->tuning.ctas_per_sm = 0;
     S->mode = mode;
     S->maxr = max_requests;
     int cur = 0;

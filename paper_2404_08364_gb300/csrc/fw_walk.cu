@@ -46,7 +46,8 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int INT_BIG = 0x7fffffff;
 constexpr int MODE_EXACT = 0, MODE_FAST = 1;
-constexpr int WIN = 128;          // staged window of N(prev) per warp (node2vec)
+constexpr int WIN = 136;          // node2vec: window of N(prev) (exact re-scans, 128) or 128 padded splitters
+constexpr int NSPL = 128;         // node2vec: splitters of a dense window
 constexpr int SW_MAX = 8;         // walk slots per warp, upper bound
 constexpr int NHUB = 4;           // hub tasks open at once per CTA
 constexpr int NSEG_MAX = 64;      // segments per hub task
@@ -59,6 +60,12 @@ constexpr int NSEG_MAX = 64;      // segments per hub task
 constexpr int kSegQuads = 4096;
 constexpr int NCHUNK_MAX = 64;    // exact warp sampler: chunk sums (d_t <= 8192)
 constexpr int NST = 3;            // TMA ring stages per warp
+// node2vec: a stage whose range, at the density of N(prev)'s loaded block,
+// would hold more than kDenseBlocks further blocks of N(prev) looks for the
+// end of its window; a window of more than kDenseMin entries is searched from
+// the stage entries' side.
+constexpr float kDenseBlocks = 3.0f;
+constexpr int kDenseMin = 512;
 constexpr int CHQ = 32;           // quads per chunk (one per lane)
 constexpr int SQ = 2 * CHQ;       // quads per stage: two chunks, lane l holds quads l and l + 32
 constexpr int ST_COL = 0, ST_W = SQ * 16, ST_ET = SQ * 32;
@@ -107,6 +114,7 @@ struct __align__(16) Smem {
     int cur[NS], prev[NS], t[NS], lim[NS], k[NS], pdeg[NS];
     int state[NS];
     HubTask hub[NHUB];
+    unsigned long long cnt[NT / 32][C_NUM];
     int abort_flag;
 };
 
@@ -376,117 +384,76 @@ __device__ __forceinline__ void bb_advance(const int32_t* __restrict__ B, int pd
     load_b128(B, pd, bb.base + 128, lane, bb.nv);
 }
 
-// node2vec membership for a stage of N(cur) in shared memory, driven from
-// B's side: the stage's valid entries colS[ia, ib) are sorted, so only the B
-// values inside [colS[ia], colS[ib-1]] can match; each such value (typically
-// a handful per stage, one per lane) binary-searches the staged entries and
-// sets its bit in the warp's 256-bit mask.  When the stage's value range,
-// at the density of the loaded block, would hold several more blocks of B,
-// one search finds the end of its window; if the window holds more than 512
-// entries of B (B much denser than this part of N(cur)), the stage is
-// answered from the entries' side instead, by lockstep binary searches of
-// each lane's values in B, and the next stage continues from the largest
-// position found.  cv[0..3] are this lane's entries at stage
-// positions 4 lane + j, cv[4..7] those at 128 + 4 lane + j; bit i of the
-// result (and of `valid`) belongs to cv[i].  Warp-collective.
-__device__ __forceinline__ unsigned members_staged(const int32_t* __restrict__ B, int pd, BBlock& bb,
-                                                   const int* __restrict__ colS, int ia, int ib,
-                                                   const int (&cv)[8], unsigned valid, int lane,
-                                                   unsigned* __restrict__ mask) {
-    if (ia >= ib || pd == 0) return 0u;
-    const int amin = colS[ia], amax = colS[ib - 1];
-    if (bb.base >= 0) {
-        // common case: the loaded block reaches past this stage and holds no
-        // value inside its range: nothing can match, one vote decides it
-        const int last = __shfl_sync(FULL, bb.v[3], 31);
-        bool in = false;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) in |= bb.v[i] >= amin && bb.v[i] <= amax;
-        if (last > amax && !__any_sync(FULL, in)) return 0u;
-    }
-    if (lane < 8) mask[lane] = 0u;
-    __syncwarp();
-    for (int guard = 0;; ++guard) {
-        if (bb.base < 0) {
-            bb_load(B, pd, lower_bound_from(B, pd, 0, amin, lane), lane, bb);
-        }
-        // (a step normally starts with B's first block already requested by
-        // the caller, overlapping that load with the first stage's copy)
-        int last = __shfl_sync(FULL, bb.v[3], 31);
-        if (last < amin) {
-            // the whole block lies below this stage: jump to the stage's range
-            bb_load(B, pd, lower_bound_from(B, pd, bb.base + 128, amin, lane), lane, bb);
-            last = __shfl_sync(FULL, bb.v[3], 31);
-        }
-        if (bb.base >= pd) break;
-        if (last <= amax && guard == 0 &&
-            (float)(amax - last) * 128.0f > 384.0f * (float)(last - __shfl_sync(FULL, bb.v[0], 0) + 1)) {
-            // the stage's range runs well past this block and, at the
-            // block's density, holds several more blocks of B: if B is dense
-            // there, search from the entries' side
-            const int ub = lower_bound_from(B, pd, bb.base + 128, amax == INT_BIG - 1 ? INT_BIG : amax + 1, lane);
-            if (ub - bb.base > 512) {
-                const int lo = bb.base;
-                unsigned f = 0;
-                int top = lo;
-#pragma unroll 1
-                for (int h = 0; h < 2; ++h) {
-                    int a[4], b[4], x[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        x[j] = h ? cv[4 + j] : cv[j];
-                        a[j] = lo;
-                        b[j] = (valid >> (4 * h + j) & 1u) ? ub : lo;
-                    }
-                    for (;;) {
-                        bool more = false;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if (a[j] < b[j]) {
-                                more = true;
-                                const int mid = (a[j] + b[j]) >> 1;
-                                if (__ldg(B + mid) < x[j]) a[j] = mid + 1;
-                                else b[j] = mid;
-                            }
-                        if (!more) break;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-                        if (valid >> (4 * h + j) & 1u) {
-                            top = max(top, a[j]);
-                            if (a[j] < ub && __ldg(B + a[j]) == x[j]) f |= 1u << (4 * h + j);
-                        }
-                }
-                // the next stage's entries are larger: its window starts at
-                // or after the largest position found here
-                bb_load(B, pd, __reduce_max_sync(FULL, top), lane, bb);
-                return f;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int bv = bb.v[i];
-            if (bv >= amin && bv <= amax) {
-                int lo = ia, hi = ib;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (colS[mid] < bv) lo = mid + 1;
-                    else hi = mid;
-                }
-                if (lo < ib && colS[lo] == bv) atomicOr(&mask[lo >> 5], 1u << (lo & 31));
-            }
-        }
-        if (last > amax) break;  // the block reaches past the stage: keep it for the next one
-        // every entry of the block is at most amax: move on to the next block
-        if (bb.base + 128 >= pd) {
-            bb.base += 128;
-            break;
-        }
-        bb_advance(B, pd, lane, bb);
-    }
-    __syncwarp();
+// Bits of the warp's 256-bit stage mask that belong to this lane's eight
+// stage entries (positions 4 lane + j and 128 + 4 lane + j).
+__device__ __forceinline__ unsigned lane_mask_bits(const unsigned* __restrict__ mask, int lane) {
     const int sh = (lane & 7) * 4;
     return ((mask[lane >> 3] >> sh) & 0xFu) | (((mask[4 + (lane >> 3)] >> sh) & 0xFu) << 4);
+}
+
+// Dense windows: B holds many more values than the stage inside the stage's
+// range, so each stage entry x > `above` searches the window B[from, end)
+// instead.  NSPL splitters B[from + (s+1) w - 1] (w = ceil((end - from) / NSPL))
+// are staged in `spl`, splitter s at index s + s / 32 so that the search's
+// power-of-two strides fall on different shared-memory banks; x's lower
+// bound lies in bracket s = the number of splitters below x, found by a
+// branch-free search in shared memory, and a binary search of that bracket
+// in global memory finishes it (log2 w dependent loads instead of
+// log2(end - from)), the lane's eight entries in lockstep.  Returns this
+// lane's hit bits in the low word and, in the high word, the largest lower
+// bound found (the next stage's window starts at or after it).
+// Warp-collective.
+__device__ __forceinline__ unsigned long long dense_members(const int32_t* __restrict__ B, int end, int from, int above,
+                                                         int4 c_lo, int4 c_hi, unsigned valid, int lane,
+                                                         int* __restrict__ spl) {
+    const int cv[8] = {c_lo.x, c_lo.y, c_lo.z, c_lo.w, c_hi.x, c_hi.y, c_hi.z, c_hi.w};
+    const int w = (end - from + NSPL - 1) / NSPL;
+#pragma unroll
+    for (int i = 0; i < NSPL / 32; ++i) {
+        const int sp = 32 * i + lane;
+        spl[sp + i] = __ldg(B + min((long long)from + (long long)(sp + 1) * w - 1, (long long)end - 1));
+    }
+    __syncwarp();
+    int a[8], b[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int x = cv[j];
+        int lo = 0;
+#pragma unroll
+        for (int step = NSPL / 2; step > 0; step >>= 1) {
+            const int i = lo + step - 1;
+            if (spl[i + (i >> 5)] < x) lo += step;
+        }
+        // lo counts the splitters 0..NSPL-2 below x; when x is above them all
+        // the bracket may start past the window's end: clamp it there (x is
+        // then not in the window, and its lower bound is the end)
+        const bool want = (valid >> j & 1u) && x > above;
+        a[j] = want ? min(from + lo * w, end) : 0;
+        b[j] = want ? min(a[j] + w, end) : 0;
+    }
+    for (;;) {
+        bool more = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (a[j] < b[j]) {
+                more = true;
+                const int mid = (a[j] + b[j]) >> 1;
+                if (__ldg(B + mid) < cv[j]) a[j] = mid + 1;
+                else b[j] = mid;
+            }
+        if (!more) break;
+    }
+    unsigned f = 0;
+    int hi_pos = from;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        if (a[j] > 0) {
+            hi_pos = max(hi_pos, a[j]);
+            if (a[j] < end && __ldg(B + a[j]) == cv[j]) f |= 1u << j;
+        }
+    const int top = __reduce_max_sync(FULL, hi_pos);
+    __syncwarp();  // the splitters are rewritten by the next dense stage
+    return ((unsigned long long)(unsigned)top << 32) | f;
 }
 
 // One lane's four consecutive row entries (an aligned quad of the CSR
@@ -617,7 +584,7 @@ __device__ __forceinline__ long long seg_quads(long long nq, int seg_q) {
 }
 
 // A new record at row entry idx of weight w (uniform across the warp).
-__device__ __noinline__ WarpRes warp_record(WarpRes r, int idx, float w, uint64_t seed, uint64_t qid, uint32_t t,
+__device__ __forceinline__ WarpRes warp_record(WarpRes r, int idx, float w, uint64_t seed, uint64_t qid, uint32_t t,
                                             uint32_t stream) {
     uint32_t a, b;
     if (r.has_spare) {
@@ -633,23 +600,25 @@ __device__ __noinline__ WarpRes warp_record(WarpRes r, int idx, float w, uint64_
         r.has_spare = 1;
     }
     const float u1 = unit_open(a), u2 = unit_open(b);
+    // -log u by the fast intrinsic (u is at least 2^-24, well inside its
+    // accurate range); the conditioned draw keeps log1pf/expm1f, whose
+    // arguments are tiny once many entries have been seen
     float e;
-    if (isinf(r.tau)) e = -logf(u1);
+    if (isinf(r.tau)) e = -__logf(u1);
     else e = -log1pf(u1 * expm1f(-w * r.tau));
-    r.tau = e / w;
+    r.tau = __fdividef(e, w);
     r.sel = idx;
-    r.Xh = -logf(u2) / r.tau;
+    r.Xh = __fdividef(-__logf(u2), r.tau);
     r.Xl = 0.0f;
     return r;
 }
 
-// Offer one stage: lane `lane` holds the entries of row indices e0 + j
-// (w[j], j < 4) and e0 + 124 + j (w[j], j >= 4), i.e. its quad of each
-// chunk of the stage.  Entries are visited lane by lane, j ascending: any
-// fixed order gives the same law.
-__device__ __forceinline__ void warp_offer_stage(WarpRes& R, const float (&w)[8], int e0, int lane, uint64_t seed,
-                                                 uint64_t qid, uint32_t t, uint32_t stream) {
-    const float own = ((w[0] + w[1]) + (w[2] + w[3])) + ((w[4] + w[5]) + (w[6] + w[7]));
+// A record falls inside a stage: find every record there, in visiting order
+// (lane by lane, j ascending), and leave R with the skip budget past the
+// stage.  `own` is this lane's weight total.
+__device__ __forceinline__ WarpRes stage_records(WarpRes R, float4 wa, float4 wb, float own, int e0, int lane,
+                                              uint64_t seed, uint64_t qid, uint32_t t, uint32_t stream) {
+    const float w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
     float incl = own;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -657,14 +626,7 @@ __device__ __forceinline__ void warp_offer_stage(WarpRes& R, const float (&w)[8]
         if (lane >= o) incl += n;
     }
     const float tot = __shfl_sync(FULL, incl, 31);
-    if (R.Xh - tot + R.Xl > 0.0f) {  // no record in this stage (the common case)
-        // X -= tot with the rounding error kept (Fast2Sum: |Xh| > tot here)
-        const float sh = R.Xh - tot;
-        R.Xl += (R.Xh - sh) - tot;
-        R.Xh = sh;
-        return;
-    }
-    // a record falls in this stage: running sums in visiting order
+    // running sums in visiting order
     float cum[8];
     cum[0] = (incl - own) + w[0];
 #pragma unroll
@@ -680,7 +642,7 @@ __device__ __forceinline__ void warp_offer_stage(WarpRes& R, const float (&w)[8]
         if (!m) {
             R.Xh = target - tot;
             R.Xl = 0.0f;
-            return;
+            return R;
         }
         const int L = __ffs(m) - 1;
         float wj = 0.0f, cj = 0.0f;
@@ -698,6 +660,29 @@ __device__ __forceinline__ void warp_offer_stage(WarpRes& R, const float (&w)[8]
         R = warp_record(R, idx, wr, seed, qid, t, stream);
         target = cr + R.Xh;
     }
+}
+
+// Offer one stage: lane `lane` holds the entries of row indices e0 + j
+// (w[j], j < 4) and e0 + 124 + j (w[j], j >= 4), i.e. its quad of each
+// chunk of the stage.  Entries are visited lane by lane, j ascending: any
+// fixed order gives the same law.  The stage total comes from an xor
+// butterfly, whose pairwise sums are the same in every lane (a + b = b + a
+// in IEEE arithmetic), so the warp's reservoir state stays uniform.
+__device__ __forceinline__ void warp_offer_stage(WarpRes& R, const float (&w)[8], int e0, int lane, uint64_t seed,
+                                                 uint64_t qid, uint32_t t, uint32_t stream) {
+    const float own = ((w[0] + w[1]) + (w[2] + w[3])) + ((w[4] + w[5]) + (w[6] + w[7]));
+    float tot = own;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(FULL, tot, o);
+    if (R.Xh - tot + R.Xl > 0.0f) {  // no record in this stage (the common case)
+        // X -= tot with the rounding error kept (Fast2Sum: |Xh| > tot here)
+        const float sh = R.Xh - tot;
+        R.Xl += (R.Xh - sh) - tot;
+        R.Xh = sh;
+        return;
+    }
+    R = stage_records(R, make_float4(w[0], w[1], w[2], w[3]), make_float4(w[4], w[5], w[6], w[7]), own, e0, lane,
+                      seed, qid, t, stream);
 }
 
 // Pick inside one lane's quad: smallest j whose prefix exceeds rr.
@@ -766,6 +751,304 @@ __device__ __forceinline__ void stage_quad(const StepCtx& c, const unsigned char
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fast mode: the lean range scan.  Used for every range whose stages can all
+// be copied by TMA (everything but the very end of the CSR arrays).  A stage
+// costs: one barrier wait, four 16-byte shared loads per lane, the weight
+// rule, the reservoir's skip test (one butterfly sum) and lane 0's copy of a
+// later stage.  Rows are masked only in a range's first and last stage.
+// node2vec tracks `nb`, the smallest value of N(prev) above every entry seen
+// so far (INT_MIN: not known yet), so that a stage with nb > its largest
+// entry — no value of N(prev) inside its range — needs no membership work.
+// ---------------------------------------------------------------------------
+
+// Lane 0: copy the first ne entries (a multiple of 16, possibly 0) of a
+// stage into ring slot st.
+__device__ __forceinline__ void issue_stage_fast(WarpPipe& P, int st, const int32_t* cs, const float* ws,
+                                                 const int8_t* es, uint32_t ne, bool labels) {
+    unsigned char* b = P.buf + st * STAGE_BYTES;
+    if (ne == 0) {
+        mbar_arrive(&P.bar[st]);
+        return;
+    }
+    mbar_arrive_expect_tx(&P.bar[st], ne * 8 + (labels ? ne : 0));
+    tma_load_1d(b + ST_COL, cs, ne * 4, &P.bar[st]);
+    tma_load_1d(b + ST_W, ws, ne * 4, &P.bar[st]);
+    if (labels) tma_load_1d(b + ST_ET, es, ne, &P.bar[st]);
+}
+
+// Entries to copy of stage k of a range: whole 16-entry groups, and for the
+// range's last stage, when it runs into the end of the CSR arrays, only the
+// groups that lie inside them (stage_tail_fill loads the rest).
+__device__ __forceinline__ uint32_t stage_copy_entries(long long m, long long e0, int nq) {
+    const long long ne = 4ll * ((nq + 3) & ~3);
+    return (uint32_t)(e0 + ne <= m ? ne : ((m - e0) >> 4) << 4);
+}
+
+// The end of the CSR arrays: the entries [e0 + from, e0 + to) of a stage
+// (to - from < 16 + 4 * SQ) that no copy brought in, by plain loads into the
+// stage buffer b.  Out of line: it runs only for the last rows of the graph.
+__device__ __noinline__ void stage_tail_fill(const int32_t* __restrict__ col, const float* __restrict__ w,
+                                             const int8_t* __restrict__ et, unsigned char* b, long long e0, int from,
+                                             int to, int lane) {
+    for (int e = from + lane; e < to; e += 32) {
+        reinterpret_cast<int*>(b + ST_COL)[e] = __ldg(col + e0 + e);
+        reinterpret_cast<float*>(b + ST_W)[e] = __ldg(w + e0 + e);
+        if (et) reinterpret_cast<int8_t*>(b + ST_ET)[e] = __ldg(et + e0 + e);
+    }
+    __syncwarp();
+}
+
+// Value at position pos (< 128) of a loaded block of B.  Warp-collective:
+// every lane takes part in the shuffles, each with its own pos.
+__device__ __forceinline__ int block_value(const BBlock& bb, int pos) {
+    const int src = pos & 31, ii = pos >> 5;
+    const int x0 = __shfl_sync(FULL, bb.v[0], src), x1 = __shfl_sync(FULL, bb.v[1], src);
+    const int x2 = __shfl_sync(FULL, bb.v[2], src), x3 = __shfl_sync(FULL, bb.v[3], src);
+    return ii == 0 ? x0 : (ii == 1 ? x1 : (ii == 2 ? x2 : x3));
+}
+
+// Stage position of value x among the stage entries, or -1.  The stage is
+// held in registers: lane l has entries 4l..4l+3 in cv[0..3] and
+// 128+4l..128+4l+3 in cv[4..7], in ascending order over the whole stage
+// (entries outside the row are INT_MIN before it and INT_BIG after it).
+// x picks its half by a127 (entry 127), then the first quad of that half
+// whose largest entry is >= x by a five-step search over the lanes'
+// registers with shuffles (no shared-memory traffic, so no bank
+// conflicts), and compares x with that quad's four entries, read from the
+// staged copy colS; positions outside [ia, ib) do not count.
+// Warp-collective.
+__device__ __forceinline__ int stage_find(const int (&cv)[8], int a127, const int* __restrict__ colS, int ia, int ib,
+                                          int x) {
+    const bool hi = x > a127;
+    int q = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int i = q + step - 1;
+        const int s3 = __shfl_sync(FULL, cv[3], i), s7 = __shfl_sync(FULL, cv[7], i);
+        if ((hi ? s7 : s3) < x) q += step;
+    }
+    const int p = (hi ? 4 * CHQ : 0) + 4 * q;
+    const int4 v = *reinterpret_cast<const int4*>(colS + p);
+    // only entries of the row count (the quad may also hold entries of the
+    // neighbouring rows, with any values)
+    const unsigned in = (unsigned)(ib - p) <= 4u ? ((1u << (ib - p)) - 1u) : (p < ib ? 0xFu : 0u);
+    const unsigned ok = in & (p >= ia ? 0xFu : (ia - p < 4 ? (0xFu << (ia - p)) : 0u));
+    const unsigned eq = (v.x == x ? 1u : 0u) | (v.y == x ? 2u : 0u) | (v.z == x ? 4u : 0u) | (v.w == x ? 8u : 0u);
+    const unsigned hit = eq & ok;
+    return hit ? p + __ffs(hit) - 1 : -1;
+}
+
+// Membership of one stage's entries in N(prev) = B when some value of B may
+// fall inside the stage's range [amin, amax] = [colS[ia], colS[ib-1]].  The
+// values of B inside the range form one run of the loaded 128-entry block
+// (and maybe of the blocks after it); the run is handed out 64 values per
+// round, at most two per lane, each located in the stage by stage_find, and every hit
+// sets its bit in the warp's 256-bit mask.  If the range runs past the block
+// and, at the block's density, would hold several more blocks, a search finds
+// where it ends, and a window of more than kDenseMin values is answered from
+// the entries' side (dense_members).  cv: this lane's entries, ordered as
+// stage_find needs them.  Returns this lane's bits (bit j: entry cv[j]) in
+// the low word and, in the high word, the first value of B above amax (or a
+// value below it, or INT_MIN when not known: the next stage then looks
+// again).  Warp-collective.
+__device__ __forceinline__ unsigned long long stage_members(const int32_t* __restrict__ B, int pd, BBlock& bb,
+                                                         const int* __restrict__ colS, int ia, int ib, int amin,
+                                                         int amax, const int (&cv)[8], unsigned valid, int lane,
+                                                         unsigned* __restrict__ mask, int* __restrict__ spl) {
+    if (bb.base < 0) bb_load(B, pd, lower_bound_from(B, pd, 0, amin, lane), lane, bb);
+    int last = __shfl_sync(FULL, bb.v[3], 31);
+    if (last < amin) {
+        // the whole block lies below this stage: jump to the stage's range
+        bb_load(B, pd, lower_bound_from(B, pd, bb.base + 128, amin, lane), lane, bb);
+        last = __shfl_sync(FULL, bb.v[3], 31);
+    }
+    const int a127 = __shfl_sync(FULL, cv[3], 31);
+    if (lane < 8) mask[lane] = 0u;
+    __syncwarp();
+    bool checked = false;
+    int nb = INT_BIG;
+    while (bb.base < pd) {
+        // positions [p0, p1) of the block hold the values inside [amin, amax]
+        int nge = 0, nle = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            nge += __popc(__ballot_sync(FULL, bb.v[i] >= amin));
+            nle += __popc(__ballot_sync(FULL, bb.v[i] <= amax));
+        }
+        const int p0 = 128 - nge, p1 = nle;
+        for (int r = p0; r < p1; r += 64) {
+            const int pa = r + lane;
+            const int ha = stage_find(cv, a127, colS, ia, ib, block_value(bb, pa));
+            if (pa < p1 && ha >= 0) atomicOr(&mask[ha >> 5], 1u << (ha & 31));
+            if (r + 32 < p1) {
+                const int pb = r + 32 + lane;
+                const int hb = stage_find(cv, a127, colS, ia, ib, block_value(bb, pb));
+                if (pb < p1 && hb >= 0) atomicOr(&mask[hb >> 5], 1u << (hb & 31));
+            }
+        }
+        if (p1 < 128) {
+            nb = block_value(bb, p1);  // the block reaches past the stage: the next value of B
+            break;
+        }
+        // every value of the block is at most amax: the window goes on
+        if (bb.base + 128 >= pd) {
+            bb.base += 128;
+            break;
+        }
+        const int first = __shfl_sync(FULL, bb.v[0], 0);
+        if (!checked && (float)(amax - last) * 128.0f > kDenseBlocks * 128.0f * (float)(last - first + 1)) {
+            checked = true;
+            const int from = bb.base + 128;
+            const int ub = lower_bound_from(B, pd, from, amax + 1, lane);
+            if (ub - from > kDenseMin) {
+                const unsigned long long dm =
+                    dense_members(B, ub, from, last, make_int4(cv[0], cv[1], cv[2], cv[3]),
+                                  make_int4(cv[4], cv[5], cv[6], cv[7]), valid, lane, spl);
+                const unsigned f = (unsigned)dm;
+                bb_load(B, pd, (int)(dm >> 32), lane, bb);
+                __syncwarp();
+                return ((unsigned long long)(unsigned)INT_MIN << 32) | (f | lane_mask_bits(mask, lane));
+            }
+        }
+        bb_advance(B, pd, lane, bb);
+        last = __shfl_sync(FULL, bb.v[3], 31);
+    }
+    __syncwarp();
+    return ((unsigned long long)(unsigned)nb << 32) | lane_mask_bits(mask, lane);
+}
+
+// Scan quads [qa, qb) of the row [c.beg, c.beg + c.d) in fast mode: weights
+// with the rule's factors, offered to the warp's reservoir R drawing from
+// random stream rng_stream.  False if a copy never landed.  Warp-collective.
+__device__ __forceinline__ bool scan_range_fast(const GraphDev& g, const StepCtx& c, long long qa, long long qb,
+                                                int lane, int* __restrict__ win, WarpPipe& P, WarpRes& R,
+                                                uint32_t rng_stream, uint64_t seed, uint64_t qid, uint32_t t) {
+    const int nqt = (int)(qb - qa);                       // quads in the range
+    const int nst = (nqt + SQ - 1) / SQ;
+    const bool labels = c.algo == FW_METAPATH;
+    const bool n2v = c.algo == FW_NODE2VEC && c.prev >= 0;
+    const int r_a = (int)((qa << 2) - c.beg);             // row index of the range's first staged entry
+    const int lim = (int)min((long long)c.d, (qb << 2) - c.beg);  // entries at or past lim are outside
+    const int32_t* cs = g.col + (qa << 2);
+    const float* ws = g.w_f32 + (qa << 2);
+    const int8_t* es = labels ? g.etype + (qa << 2) : nullptr;
+    if (lane == 0) {
+        int ist = P.st;
+        uint32_t iph = P.ph;
+        for (int k = 0; k < nst && k < NST; ++k) {
+            const int nq = min(SQ, nqt - k * SQ);
+            issue_stage_fast(P, ist, cs + k * 4 * SQ, ws + k * 4 * SQ, es ? es + k * 4 * SQ : nullptr,
+                             stage_copy_entries(g.m, (qa << 2) + k * 4 * SQ, nq), labels);
+            ring_next(ist, iph);
+        }
+    }
+    // whether the last stage runs into the end of the CSR arrays
+    const bool tail = (qa + (long long)(nst - 1) * SQ + ((nqt - (nst - 1) * SQ + 3) & ~3)) * 4 > g.m;
+    const int32_t* B = g.col + c.pbeg;
+    BBlock bb;
+    bb.base = -1;
+    int nb = INT_MIN;
+    if (n2v && qa == ((c.beg >> 2) & ~3ll)) {
+        // a whole row (or its first segment): start loading N(prev)'s first
+        // block now, while the first stage is still on its way
+        bb_load(B, c.pdeg, 0, lane, bb);
+    }
+    for (int k = 0; k < nst; ++k) {
+        const int st = P.st;
+        if (!mbar_try_wait(&P.bar[st], P.ph)) {
+            const bool ok = mbar_wait_bounded(&P.bar[st], P.ph);
+            if (!__all_sync(FULL, ok)) {
+                // let the copies already issued land before giving up
+                if (lane == 0) {
+                    int dst = st;
+                    uint32_t dph = P.ph;
+                    for (int kk = k + 1; kk < nst && kk < k + NST; ++kk) {
+                        ring_next(dst, dph);
+                        mbar_wait_bounded(&P.bar[dst], dph);
+                    }
+                }
+                return false;
+            }
+        }
+        unsigned char* b = P.buf + st * STAGE_BYTES;
+        if (tail && k == nst - 1) {
+            const long long e0 = (qa << 2) + k * 4 * SQ;
+            const int nq = nqt - k * SQ;
+            stage_tail_fill(g.col, g.w_f32, labels ? g.etype : nullptr, b, e0,
+                            (int)stage_copy_entries(g.m, e0, nq), (int)min(4ll * nq, g.m - e0), lane);
+        }
+        const int4 c0 = *reinterpret_cast<const int4*>(b + ST_COL + lane * 16);
+        const int4 c1 = *reinterpret_cast<const int4*>(b + ST_COL + CHQ * 16 + lane * 16);
+        const float4 w0 = *reinterpret_cast<const float4*>(b + ST_W + lane * 16);
+        const float4 w1 = *reinterpret_cast<const float4*>(b + ST_W + CHQ * 16 + lane * 16);
+        int cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        float wv[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+        const int r0 = r_a + k * (4 * SQ);
+        const bool edge = r0 < 0 || r0 + 4 * SQ > lim;
+        unsigned valid = 0xFFu;
+        if (edge) {
+            // the range's first or last stage: entries outside the row are out
+            valid = 0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int rel = r0 + 4 * lane + j + (j >= 4 ? 4 * CHQ - 4 : 0);
+                if ((unsigned)rel < (unsigned)lim) {
+                    valid |= 1u << j;
+                } else {
+                    cv[j] = rel < 0 ? INT_MIN : INT_BIG;  // keeps the stage's entries in ascending order
+                    wv[j] = 0.0f;
+                }
+            }
+        }
+        if (labels) {
+            const int e0 = *reinterpret_cast<const int*>(b + ST_ET + lane * 4);
+            const int e1 = *reinterpret_cast<const int*>(b + ST_ET + CHQ * 4 + lane * 4);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if ((int)(int8_t)((j < 4 ? e0 : e1) >> (8 * (j & 3))) != c.want) wv[j] = 0.0f;
+        }
+        if (n2v) {
+            const int* colS = reinterpret_cast<const int*>(b + ST_COL);
+            int ia = 0, ib = 4 * SQ, amin, amax;
+            if (edge) {
+                ia = max(0, -r0);
+                ib = min(4 * SQ, lim - r0);
+                amin = colS[ia];
+                amax = colS[ib - 1];
+            } else {
+                amin = __shfl_sync(FULL, cv[0], 0);
+                amax = __shfl_sync(FULL, cv[7], 31);
+            }
+            unsigned mem = 0;
+            if (nb <= amax) {
+                const unsigned long long r =
+                    stage_members(B, c.pdeg, bb, colS, ia, ib, amin, amax, cv, valid, lane, P.mask, win);
+                mem = (unsigned)r;
+                nb = (int)(unsigned)(r >> 32);
+            }
+            const bool pin = c.prev >= amin && c.prev <= amax;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float f = (mem >> j & 1u) ? c.ff1 : c.ff2;
+                if (pin && cv[j] == c.prev) f = c.ff0;
+                wv[j] *= f;
+            }
+        }
+        __syncwarp();  // every lane is done with the stage: it may be refilled
+        if (lane == 0 && k + NST < nst) {
+            const int kn = k + NST;
+            const int nq = min(SQ, nqt - kn * SQ);
+            issue_stage_fast(P, st, cs + kn * 4 * SQ, ws + kn * 4 * SQ, es ? es + kn * 4 * SQ : nullptr,
+                             stage_copy_entries(g.m, (qa << 2) + kn * 4 * SQ, nq), labels);
+        }
+        ring_next(P.st, P.ph);
+        warp_offer_stage(R, wv, r0 + 4 * lane, lane, seed, qid, t, rng_stream);
+    }
+    return true;
+}
+
+
 // Stream quads [qa, qb) (qa a multiple of 4) of the row [c.beg, end) through
 // the warp's TMA ring, NST - 1 stages ahead: weights with the node2vec
 // factors applied, then (fast) the warp's reservoir drawing from random
@@ -796,6 +1079,7 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
     int pos = 0;
     BBlock bb;
     bb.base = -1;
+    int nb = INT_MIN;  // smallest value of N(prev) above the entries seen so far (INT_MIN: not known)
     const bool n2v = c.algo == FW_NODE2VEC && c.prev >= 0;
     if (n2v && qa == ((c.beg >> 2) & ~3ll)) {
         // a whole row (or its first segment): start loading N(prev)'s first
@@ -838,9 +1122,20 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
                 // staged entries [ia, ib) belong to this range of the row
                 const int ia = max(0, -r0);
                 const int ib = min(4 * SQ, lim - r0);
-                const int cv[8] = {h0.c[0], h0.c[1], h0.c[2], h0.c[3], h1.c[0], h1.c[1], h1.c[2], h1.c[3]};
-                const unsigned mem = members_staged(g.col + c.pbeg, c.pdeg, bb, reinterpret_cast<const int*>(b + ST_COL),
-                                                    ia, ib, cv, h0.valid | (h1.valid << 4), lane, P.mask);
+                // the stage's entries in ascending order: INT_MIN before the row, INT_BIG after it
+                int cv[8] = {h0.c[0], h0.c[1], h0.c[2], h0.c[3], h1.c[0], h1.c[1], h1.c[2], h1.c[3]};
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (4 * lane + j + (j >= 4 ? 4 * CHQ - 4 : 0) < ia) cv[j] = INT_MIN;
+                const int* colS = reinterpret_cast<const int*>(b + ST_COL);
+                unsigned mem = 0;
+                if (ia < ib && nb <= colS[ib - 1]) {
+                    const unsigned long long rm = stage_members(g.col + c.pbeg, c.pdeg, bb, colS, ia, ib, colS[ia],
+                                                                colS[ib - 1], cv, h0.valid | (h1.valid << 4), lane,
+                                                                P.mask, win);
+                    mem = (unsigned)rm;
+                    nb = (int)(unsigned)(rm >> 32);
+                }
                 n2v_factors<MODE>(c, h0, mem & 0xFu);
                 n2v_factors<MODE>(c, h1, mem >> 4);
             }
@@ -926,9 +1221,10 @@ __device__ __forceinline__ int find_req(const ReqDev* __restrict__ reqs, int n_r
     return lo;
 }
 
-// Per-warp counters, kept by lane 0 and flushed at exit.
+// Per-warp counters, kept by lane 0 in the warp's shared-memory row (not in
+// registers: the scan loop needs them) and flushed at exit.
 struct Counters {
-    unsigned long long v[C_NUM];
+    unsigned long long* v;
     __device__ __forceinline__ void clear() {
 #pragma unroll
         for (int i = 0; i < C_NUM; ++i) v[i] = 0;
@@ -1128,7 +1424,8 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
     __syncthreads();
 
     Counters cnt;
-    cnt.clear();
+    cnt.v = sm.cnt[warp];
+    if (lane == 0) cnt.clear();
     const int s0 = warp * SW_MAX;
     bool exhausted = false;
     int rr = 0;
@@ -1403,8 +1700,13 @@ __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, cons
         bool scanned = true;
         for (long long sa = qa; sa < qb; sa += sq) {
             res.init();
-            if (!scan_range<MODE>(g, c, sa, min(qb, sa + sq), end, lane, win, P, res, lane_sum, sums, stream, seed,
-                                  qid, t)) {
+            const long long sb = min(qb, sa + sq);
+            bool ok;
+            if constexpr (MODE == MODE_FAST)
+                ok = scan_range_fast(g, c, sa, sb, lane, win, P, res, stream, seed, qid, t);
+            else
+                ok = scan_range<MODE>(g, c, sa, sb, end, lane, win, P, res, lane_sum, sums, stream, seed, qid, t);
+            if (!ok) {
                 scanned = false;
                 break;
             }
@@ -1517,12 +1819,12 @@ cudaError_t launch_serve_one(const GraphDev& g, const ServeDev& sv, Scratch* scr
 
 }  // namespace
 
-Tuning default_tuning() { return Tuning{128, 16, 16384, 0}; }
+Tuning default_tuning() { return Tuning{512, 64, 16384, 0}; }
 
 Tuning sanitize_tuning(Tuning t) {
     const Tuning d = default_tuning();
     if (t.block_threads != 128 && t.block_threads != 256 && t.block_threads != 512) t.block_threads = d.block_threads;
-    if (t.slots <= 0) t.slots = d.slots;
+    if (t.slots <= 0) t.slots = 4 * (t.block_threads / 32);  // four walks per warp
     if (t.slots > (t.block_threads / 32) * SW_MAX) t.slots = (t.block_threads / 32) * SW_MAX;
     if (t.d_warp <= 0) t.d_warp = d.d_warp;
     if (t.d_warp < 128) t.d_warp = 128;
