@@ -149,14 +149,15 @@ def profiled_traffic_ratio(workload):
     the kernel as it is now; else None."""
     import glob
     import re
-    pat = re.compile(r"^traffic-per-algorithmic-byte: ([0-9.]+) \(workload (\S+), sources ([0-9a-f]+)\)")
+    pat = re.compile(r"^traffic-per-algorithmic-byte: ([0-9.]+) \(workload (\S+), sources ([0-9a-f]+)"
+                     r"(?:, stands for (\S+))?\)")
     cur = kernel_sources_hash()
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as f:
             for line in f:
                 m = pat.match(line.strip())
-                if m and m.group(2) == workload and m.group(3) == cur:
-                    return float(m.group(1)), os.path.relpath(path, ROOT)
+                if m and workload in (m.group(2), m.group(4)) and m.group(3) == cur:
+                    return float(m.group(1)), os.path.relpath(path, ROOT), m.group(2)
     return None
 
 
@@ -746,7 +747,7 @@ def main():
                      "frac_vs_8tbs": achieved / NOMINAL_HBM_GBS,
                      "traffic": prof[0] * algo_bytes_per_launch if prof else None,
                      "traffic_source": (f"{prof[1]}: ncu dram__bytes_read.sum + dram__bytes_write.sum of one "
-                                        f"full-size launch per algorithmic byte ({prof[0]}), times this run's "
+                                        f"launch of {prof[2]} per algorithmic byte ({prof[0]}), times this run's "
                                         f"algorithmic bytes per launch") if prof else
                                        "no ncu capture of the kernel as built now",
                      "peak_kind": f"{peak_kind} (copy bandwidth)",

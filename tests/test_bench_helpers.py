@@ -17,13 +17,16 @@ def test_traffic_ratio_tied_to_sources(tmp_path, monkeypatch):
     prof.mkdir()
     (prof / "x.md").write_text(
         "text\ntraffic-per-algorithmic-byte: 1.5 (workload wl_a, sources %s)\n"
-        "traffic-per-algorithmic-byte: 9.0 (workload wl_b, sources 0000000000000000)\n" % cur)
+        "traffic-per-algorithmic-byte: 9.0 (workload wl_b, sources 0000000000000000)\n"
+        "traffic-per-algorithmic-byte: 1.2 (workload wl_small, sources %s, stands for wl_big)\n" % (cur, cur))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     # the sources are hashed from ROOT: point it back at the repository for them
     monkeypatch.setattr(bench, "kernel_sources_hash", lambda: cur)
     assert bench.profiled_traffic_ratio("wl_a")[0] == 1.5
     assert bench.profiled_traffic_ratio("wl_b") is None      # captured on other sources
     assert bench.profiled_traffic_ratio("wl_c") is None      # never captured
+    # a small case captured for a workload too large to capture stands in for it
+    assert bench.profiled_traffic_ratio("wl_big")[:1] == (1.2,) and bench.profiled_traffic_ratio("wl_big")[2] == "wl_small"
 
 
 def test_source_hash_is_stable_and_short():
