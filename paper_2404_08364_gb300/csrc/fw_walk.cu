@@ -65,7 +65,7 @@ constexpr int NST = 3;            // TMA ring stages per warp
 // end of its window; a window of more than kDenseMin entries is searched from
 // the stage entries' side.
 constexpr float kDenseBlocks = 3.0f;
-constexpr int kDenseMin = 512;
+constexpr int kDenseMin = 256;
 constexpr int CHQ = 32;           // quads per chunk (one per lane)
 constexpr int SQ = 2 * CHQ;       // quads per stage: two chunks, lane l holds quads l and l + 32
 constexpr int ST_COL = 0, ST_W = SQ * 16, ST_ET = SQ * 32;
@@ -830,12 +830,13 @@ __device__ __forceinline__ int stage_find(const int (&cv)[8], int a127, const in
     }
     const int p = (hi ? 4 * CHQ : 0) + 4 * q;
     const int4 v = *reinterpret_cast<const int4*>(colS + p);
-    // only entries of the row count (the quad may also hold entries of the
-    // neighbouring rows, with any values)
-    const unsigned in = (unsigned)(ib - p) <= 4u ? ((1u << (ib - p)) - 1u) : (p < ib ? 0xFu : 0u);
-    const unsigned ok = in & (p >= ia ? 0xFu : (ia - p < 4 ? (0xFu << (ia - p)) : 0u));
-    const unsigned eq = (v.x == x ? 1u : 0u) | (v.y == x ? 2u : 0u) | (v.z == x ? 4u : 0u) | (v.w == x ? 8u : 0u);
-    const unsigned hit = eq & ok;
+    unsigned hit = (v.x == x ? 1u : 0u) | (v.y == x ? 2u : 0u) | (v.z == x ? 4u : 0u) | (v.w == x ? 8u : 0u);
+    if (ia > 0 || ib < 4 * SQ) {
+        // an edge stage: only entries of the row count (the quad may also
+        // hold entries of the neighbouring rows, with any values)
+        const unsigned in = (unsigned)(ib - p) <= 4u ? ((1u << (ib - p)) - 1u) : (p < ib ? 0xFu : 0u);
+        hit &= in & (p >= ia ? 0xFu : (ia - p < 4 ? (0xFu << (ia - p)) : 0u));
+    }
     return hit ? p + __ffs(hit) - 1 : -1;
 }
 
@@ -877,15 +878,11 @@ __device__ __forceinline__ unsigned long long stage_members(const int32_t* __res
             nle += __popc(__ballot_sync(FULL, bb.v[i] <= amax));
         }
         const int p0 = 128 - nge, p1 = nle;
-        for (int r = p0; r < p1; r += 64) {
+#pragma unroll 1
+        for (int r = p0; r < p1; r += 32) {
             const int pa = r + lane;
             const int ha = stage_find(cv, a127, colS, ia, ib, block_value(bb, pa));
             if (pa < p1 && ha >= 0) atomicOr(&mask[ha >> 5], 1u << (ha & 31));
-            if (r + 32 < p1) {
-                const int pb = r + 32 + lane;
-                const int hb = stage_find(cv, a127, colS, ia, ib, block_value(bb, pb));
-                if (pb < p1 && hb >= 0) atomicOr(&mask[hb >> 5], 1u << (hb & 31));
-            }
         }
         if (p1 < 128) {
             nb = block_value(bb, p1);  // the block reaches past the stage: the next value of B
