@@ -59,7 +59,7 @@ constexpr int NSEG_MAX = 64;      // segments per hub task
 // on the threshold d_t or the launch shape.
 constexpr int kSegQuads = 4096;
 constexpr int NCHUNK_MAX = 64;    // exact warp sampler: chunk sums (d_t <= 8192)
-constexpr int NST = 3;            // TMA ring stages per warp
+constexpr int NST = 2;            // TMA ring stages per warp (the next stage lands while one is read)
 // node2vec: a stage whose range, at the density of N(prev)'s loaded block,
 // would hold more than kDenseBlocks further blocks of N(prev) looks for the
 // end of its window; a window of more than kDenseMin entries is searched from
@@ -207,7 +207,7 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
 struct WarpPipe {
     unsigned char* buf;
     unsigned long long* bar;
-    unsigned* mask;  // node2vec membership bits of the current stage (8 words)
+    unsigned* mask;  // node2vec membership of the current stage: one byte per entry (64 words)
     int st;
     uint32_t ph;
 };
@@ -384,11 +384,14 @@ __device__ __forceinline__ void bb_advance(const int32_t* __restrict__ B, int pd
     load_b128(B, pd, bb.base + 128, lane, bb.nv);
 }
 
-// Bits of the warp's 256-bit stage mask that belong to this lane's eight
+// Bits of the warp's stage membership bytes that belong to this lane's eight
 // stage entries (positions 4 lane + j and 128 + 4 lane + j).
 __device__ __forceinline__ unsigned lane_mask_bits(const unsigned* __restrict__ mask, int lane) {
-    const int sh = (lane & 7) * 4;
-    return ((mask[lane >> 3] >> sh) & 0xFu) | (((mask[4 + (lane >> 3)] >> sh) & 0xFu) << 4);
+    // the four bytes of a quad (each 0 or 1) gathered into four bits: the
+    // multiplier moves byte j's low bit to bit 24 + j, and no two partial
+    // products land on the same bit, so nothing carries into bits 24..27
+    const unsigned b0 = mask[lane] & 0x01010101u, b1 = mask[CHQ + lane] & 0x01010101u;
+    return ((b0 * 0x01020408u) >> 24) | (((b1 * 0x01020408u) >> 24) << 4);
 }
 
 // Dense windows: B holds many more values than the stage inside the stage's
@@ -808,44 +811,35 @@ __device__ __forceinline__ int block_value(const BBlock& bb, int pos) {
     return ii == 0 ? x0 : (ii == 1 ? x1 : (ii == 2 ? x2 : x3));
 }
 
-// Stage position of value x among the stage entries, or -1.  The stage is
-// held in registers: lane l has entries 4l..4l+3 in cv[0..3] and
-// 128+4l..128+4l+3 in cv[4..7], in ascending order over the whole stage
-// (entries outside the row are INT_MIN before it and INT_BIG after it).
-// x picks its half by a127 (entry 127), then the first quad of that half
-// whose largest entry is >= x by a five-step search over the lanes'
-// registers with shuffles (no shared-memory traffic, so no bank
-// conflicts), and compares x with that quad's four entries, read from the
-// staged copy colS; positions outside [ia, ib) do not count.
-// Warp-collective.
-__device__ __forceinline__ int stage_find(const int (&cv)[8], int a127, const int* __restrict__ colS, int ia, int ib,
-                                          int x) {
+// Stage position of value x among the 256 staged entries colS, or -1.  colS
+// ascends over the whole stage: the scan has overwritten the entries outside
+// the row with INT_MIN (before it) and INT_BIG (after it), which equal no
+// vertex id.  x picks its half by a127 (entry 127), then the first quad of
+// that half whose largest entry is >= x by a five-step binary search over
+// the quads' last entries in shared memory, and compares x with that quad's
+// four entries.  Per lane; x may differ between lanes.
+__device__ __forceinline__ int stage_find(int a127, const int* __restrict__ colS, int x) {
     const bool hi = x > a127;
+    const int* qmax = colS + (hi ? 4 * CHQ : 0) + 3;  // qmax[4 q] = last entry of quad q of the half
     int q = 0;
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1) {
         const int i = q + step - 1;
-        const int s3 = __shfl_sync(FULL, cv[3], i), s7 = __shfl_sync(FULL, cv[7], i);
-        if ((hi ? s7 : s3) < x) q += step;
+        if (qmax[4 * i] < x) q += step;
     }
     const int p = (hi ? 4 * CHQ : 0) + 4 * q;
     const int4 v = *reinterpret_cast<const int4*>(colS + p);
-    unsigned hit = (v.x == x ? 1u : 0u) | (v.y == x ? 2u : 0u) | (v.z == x ? 4u : 0u) | (v.w == x ? 8u : 0u);
-    if (ia > 0 || ib < 4 * SQ) {
-        // an edge stage: only entries of the row count (the quad may also
-        // hold entries of the neighbouring rows, with any values)
-        const unsigned in = (unsigned)(ib - p) <= 4u ? ((1u << (ib - p)) - 1u) : (p < ib ? 0xFu : 0u);
-        hit &= in & (p >= ia ? 0xFu : (ia - p < 4 ? (0xFu << (ia - p)) : 0u));
-    }
+    const unsigned hit = (v.x == x ? 1u : 0u) | (v.y == x ? 2u : 0u) | (v.z == x ? 4u : 0u) | (v.w == x ? 8u : 0u);
     return hit ? p + __ffs(hit) - 1 : -1;
 }
 
 // Membership of one stage's entries in N(prev) = B when some value of B may
-// fall inside the stage's range [amin, amax] = [colS[ia], colS[ib-1]].  The
-// values of B inside the range form one run of the loaded 128-entry block
-// (and maybe of the blocks after it); the run is handed out 64 values per
-// round, at most two per lane, each located in the stage by stage_find, and every hit
-// sets its bit in the warp's 256-bit mask.  If the range runs past the block
+// fall inside the stage's range [amin, amax] (its first and last entry of
+// the row).  The values of B inside the range form one run of the loaded
+// 128-entry block (and maybe of the blocks after it); the run is handed out
+// 32 values per round, one per lane, each located in the stage by stage_find,
+// and every hit sets its entry's byte in the warp's 256-byte mask (the values
+// of B are distinct, so no two lanes write the same byte).  If the range runs past the block
 // and, at the block's density, would hold several more blocks, a search finds
 // where it ends, and a window of more than kDenseMin values is answered from
 // the entries' side (dense_members).  cv: this lane's entries, ordered as
@@ -854,7 +848,7 @@ __device__ __forceinline__ int stage_find(const int (&cv)[8], int a127, const in
 // value below it, or INT_MIN when not known: the next stage then looks
 // again).  Warp-collective.
 __device__ __forceinline__ unsigned long long stage_members(const int32_t* __restrict__ B, int pd, BBlock& bb,
-                                                         const int* __restrict__ colS, int ia, int ib, int amin,
+                                                         const int* __restrict__ colS, int amin,
                                                          int amax, const int (&cv)[8], unsigned valid, int lane,
                                                          unsigned* __restrict__ mask, int* __restrict__ spl) {
     if (bb.base < 0) bb_load(B, pd, lower_bound_from(B, pd, 0, amin, lane), lane, bb);
@@ -865,7 +859,7 @@ __device__ __forceinline__ unsigned long long stage_members(const int32_t* __res
         last = __shfl_sync(FULL, bb.v[3], 31);
     }
     const int a127 = __shfl_sync(FULL, cv[3], 31);
-    if (lane < 8) mask[lane] = 0u;
+    reinterpret_cast<uint2*>(mask)[lane] = make_uint2(0u, 0u);
     __syncwarp();
     bool checked = false;
     int nb = INT_BIG;
@@ -881,8 +875,8 @@ __device__ __forceinline__ unsigned long long stage_members(const int32_t* __res
 #pragma unroll 1
         for (int r = p0; r < p1; r += 32) {
             const int pa = r + lane;
-            const int ha = stage_find(cv, a127, colS, ia, ib, block_value(bb, pa));
-            if (pa < p1 && ha >= 0) atomicOr(&mask[ha >> 5], 1u << (ha & 31));
+            const int ha = stage_find(a127, colS, block_value(bb, pa));
+            if (pa < p1 && ha >= 0) reinterpret_cast<unsigned char*>(mask)[ha] = 1;
         }
         if (p1 < 128) {
             nb = block_value(bb, p1);  // the block reaches past the stage: the next value of B
@@ -985,7 +979,9 @@ __device__ __forceinline__ bool scan_range_fast(const GraphDev& g, const StepCtx
         const bool edge = r0 < 0 || r0 + 4 * SQ > lim;
         unsigned valid = 0xFFu;
         if (edge) {
-            // the range's first or last stage: entries outside the row are out
+            // the range's first or last stage: entries outside the row are
+            // out; node2vec also overwrites them in the staged copy, which
+            // stage_find searches
             valid = 0;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
@@ -995,6 +991,7 @@ __device__ __forceinline__ bool scan_range_fast(const GraphDev& g, const StepCtx
                 } else {
                     cv[j] = rel < 0 ? INT_MIN : INT_BIG;  // keeps the stage's entries in ascending order
                     wv[j] = 0.0f;
+                    if (n2v) reinterpret_cast<int*>(b + ST_COL)[4 * lane + (j & 3) + (j >= 4 ? 4 * CHQ : 0)] = cv[j];
                 }
             }
         }
@@ -1020,16 +1017,21 @@ __device__ __forceinline__ bool scan_range_fast(const GraphDev& g, const StepCtx
             unsigned mem = 0;
             if (nb <= amax) {
                 const unsigned long long r =
-                    stage_members(B, c.pdeg, bb, colS, ia, ib, amin, amax, cv, valid, lane, P.mask, win);
+                    stage_members(B, c.pdeg, bb, colS, amin, amax, cv, valid, lane, P.mask, win);
                 mem = (unsigned)r;
                 nb = (int)(unsigned)(r >> 32);
             }
-            const bool pin = c.prev >= amin && c.prev <= amax;
+            if (c.prev >= amin && c.prev <= amax) {
+                // prev may sit in this stage: the return factor applies there
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float f = (mem >> j & 1u) ? c.ff1 : c.ff2;
-                if (pin && cv[j] == c.prev) f = c.ff0;
-                wv[j] *= f;
+                for (int j = 0; j < 8; ++j) {
+                    float f = (mem >> j & 1u) ? c.ff1 : c.ff2;
+                    if (cv[j] == c.prev) f = c.ff0;
+                    wv[j] *= f;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) wv[j] *= (mem >> j & 1u) ? c.ff1 : c.ff2;
             }
         }
         __syncwarp();  // every lane is done with the stage: it may be refilled
@@ -1112,7 +1114,7 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
             n2v_apply<MODE>(g, c, h0, pos, lane, win);
             n2v_apply<MODE>(g, c, h1, pos, lane, win);
         } else {
-            const unsigned char* b = P.buf + st * STAGE_BYTES;
+            unsigned char* b = P.buf + st * STAGE_BYTES;
             stage_quad<MODE>(c, b, 0, r0, lim, lane, h0);
             stage_quad<MODE>(c, b, 1, r0, lim, lane, h1);
             if (n2v) {
@@ -1121,13 +1123,19 @@ __device__ __forceinline__ bool scan_range(const GraphDev& g, const StepCtx& c, 
                 const int ib = min(4 * SQ, lim - r0);
                 // the stage's entries in ascending order: INT_MIN before the row, INT_BIG after it
                 int cv[8] = {h0.c[0], h0.c[1], h0.c[2], h0.c[3], h1.c[0], h1.c[1], h1.c[2], h1.c[3]};
+                int* colS = reinterpret_cast<int*>(b + ST_COL);
+                const unsigned vbits = h0.valid | (h1.valid << 4);
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (4 * lane + j + (j >= 4 ? 4 * CHQ - 4 : 0) < ia) cv[j] = INT_MIN;
-                const int* colS = reinterpret_cast<const int*>(b + ST_COL);
+                for (int j = 0; j < 8; ++j) {
+                    const int e = 4 * lane + (j & 3) + (j >= 4 ? 4 * CHQ : 0);
+                    if (e < ia) cv[j] = INT_MIN;
+                    // entries outside the row take their sentinel in the
+                    // staged copy too, which stage_find searches
+                    if (!(vbits >> j & 1u)) colS[e] = cv[j];
+                }
                 unsigned mem = 0;
                 if (ia < ib && nb <= colS[ib - 1]) {
-                    const unsigned long long rm = stage_members(g.col + c.pbeg, c.pdeg, bb, colS, ia, ib, colS[ia],
+                    const unsigned long long rm = stage_members(g.col + c.pbeg, c.pdeg, bb, colS, colS[ia],
                                                                 colS[ib - 1], cv, h0.valid | (h1.valid << 4), lane,
                                                                 P.mask, win);
                     mem = (unsigned)rm;
@@ -1381,7 +1389,7 @@ struct WarpSmem {
     static constexpr int SUMS_OFF = WIN_OFF + WIN * 4;
     static constexpr int BAR_OFF = SUMS_OFF + (MODE == MODE_EXACT ? NCHUNK_MAX * 8 : 0);
     static constexpr int MASK_OFF = BAR_OFF + NST * 8;
-    static constexpr int BYTES = (MASK_OFF + 32 + 127) & ~127;
+    static constexpr int BYTES = (MASK_OFF + 4 * SQ + 127) & ~127;
 };
 
 // ------------------------------------------------------------- the engine
