@@ -111,7 +111,7 @@ typedef struct {
  *   slots           walks resident per CTA: the local task pool P_L, at most
  *                   8 per warp (default 4 per warp).
  *   d_warp          degree threshold d_t: rows with d <= d_warp are sampled
- *                   by one warp, larger rows by the whole CTA (default 16384;
+ *                   by one warp, larger rows by the whole CTA (default 65536;
  *                   exact mode caps it at 8184).
  *   ctas_per_sm     persistent CTAs per SM (0 = as many as fit).
  * Zero fields mean "default".  No field changes a walk's result: exact mode is

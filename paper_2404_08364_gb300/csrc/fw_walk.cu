@@ -24,15 +24,17 @@
 //     128-entry chunk or per segment in shared memory, the second re-reads
 //     only the chunk or segment holding the crossing);
 //   fast mode: one pass of weighted reservoir sampling in exponential-race
-//     form: each lane runs Efraimidis-Spirakis reservoir sampling with
-//     exponential jumps over its entries (random draws only when its
-//     reservoir changes, O(log d) per lane), lanes and segments merged by an
-//     arg-min over race times (a 64-bit atomicMin of packed (time, index)
-//     across the warps of a hub task).
+//     form: the warp keeps one Efraimidis-Spirakis reservoir with
+//     exponential jumps per row segment (a warp sum per 256-entry stage
+//     against the remaining jump budget; random draws only where a record
+//     falls, about ln d per row), and segments are merged by an arg-min over
+//     race times (a 64-bit atomicMin of packed (time, index) across the
+//     warps of a hub task).
 //
-// Rows are streamed in 128-entry chunks (a lane holds one aligned quad of
-// four entries, 16-byte loads of columns and weights), with the next chunk's
-// loads in flight while the current one is sampled.
+// Rows are streamed in 256-entry stages (columns, weights and labels) by TMA
+// bulk copies into a two-stage shared-memory ring per warp, the next stage's
+// copy in flight while the current one is sampled; a lane reads two aligned
+// 16-byte quads per stage.
 #include <math.h>
 #include <string.h>
 
@@ -1399,12 +1401,15 @@ struct WarpSmem {
 // few registers it costs).
 constexpr int min_ctas(int nt) { return nt >= 512 ? 1 : (nt >= 256 ? 3 : 5); }
 
-template <int MODE, int NT>
+// SERVE: the served form's build (queries claimed from the request ring,
+// completion stamps, idle polling); the batch build compiles all of that
+// out, which keeps its instruction footprint smaller.
+template <int MODE, int NT, bool SERVE>
 __global__ void __launch_bounds__(NT, min_ctas(NT)) walk_kernel(GraphDev g, const __grid_constant__ ReqTable tab, int n_req,
                                                   long long total, unsigned long long* cursor,
                                                   unsigned long long* counters, int sw, int d_t, int seg_q,
                                                   ServeDev sv) {
-    const bool serving = sv.ring != nullptr;
+    constexpr bool serving = SERVE;
     const ReqDev* __restrict__ reqs = serving ? sv.ring : (tab.ext ? tab.ext : tab.r);
     __shared__ Smem<NT> sm;
     // dynamic shared memory per warp: the node2vec window (WIN ints) and, in
@@ -1768,7 +1773,7 @@ template <int MODE, int NT>
 cudaError_t launch_one(const GraphDev& g, const ReqTable& reqs, int n_req, int64_t total,
                        unsigned long long* cursor, unsigned long long* counters, const Tuning& tu,
                        cudaStream_t stream) {
-    auto kern = walk_kernel<MODE, NT>;
+    auto kern = walk_kernel<MODE, NT, false>;
     const size_t dyn = (size_t)(NT / 32) * WarpSmem<MODE>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
@@ -1795,7 +1800,7 @@ cudaError_t launch_one(const GraphDev& g, const ReqTable& reqs, int n_req, int64
 template <int MODE, int NT>
 cudaError_t launch_serve_one(const GraphDev& g, const ServeDev& sv, Scratch* scratch, const Tuning& tu,
                              cudaStream_t stream) {
-    auto kern = walk_kernel<MODE, NT>;
+    auto kern = walk_kernel<MODE, NT, true>;
     const size_t dyn = (size_t)(NT / 32) * WarpSmem<MODE>::BYTES;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
@@ -1824,7 +1829,7 @@ cudaError_t launch_serve_one(const GraphDev& g, const ServeDev& sv, Scratch* scr
 
 }  // namespace
 
-Tuning default_tuning() { return Tuning{512, 64, 16384, 0}; }
+Tuning default_tuning() { return Tuning{512, 64, 65536, 0}; }
 
 Tuning sanitize_tuning(Tuning t) {
     const Tuning d = default_tuning();

@@ -124,6 +124,7 @@ def test_T3_metapath_masked(orc):
 def test_T4_hub_block_tier(orc):
     g = cached_graph("rmat", 20)
     dg = device_graph(g)
+    dg.set_tuning(d_warp=4096)  # the max-degree row is far above d_t: the CTA sampler's tier
     cur = int((g.row_ptr[1:] - g.row_ptr[:-1]).argmax())
     nxt = _one_step(dg, "weighted", cur, -1, 0, 20240416)
     st = dg.stats()
