@@ -134,12 +134,25 @@ class ClockSampler:
 KERNEL_SOURCES = ("paper_2404_08364_gb300/csrc/fw_walk.cu", "paper_2404_08364_gb300/csrc/fw_internal.cuh")
 
 
+def _code_tokens(text):
+    """The source with its comments and whitespace runs removed: what the
+    compiler sees.  String literals are kept whole (a "//" inside one is not a
+    comment)."""
+    import re
+    tok = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/|\s+', re.S)
+    return tok.sub(lambda m: m.group(0) if m.group(0).startswith('"') else " ", text).split()
+
+
 def kernel_sources_hash():
+    """Hash of the walk kernel's sources, comments and layout excluded, so
+    that a profile stays tied to the code it was captured on and not to the
+    wording of its comments."""
     import hashlib
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            h.update(" ".join(_code_tokens(fh.read())).encode())
+        h.update(b"\0")
     return h.hexdigest()[:16]
 
 

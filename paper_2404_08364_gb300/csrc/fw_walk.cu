@@ -1396,9 +1396,10 @@ struct WarpSmem {
 
 // ------------------------------------------------------------- the engine
 
-// Resident CTAs per SM the register budget is cut for: 24 warps per SM at
-// 256 threads (the engine is latency-bound; occupancy pays more than the
-// few registers it costs).
+// Resident CTAs per SM the register budget is cut for.  The default
+// 512-thread build keeps 128 registers a thread (16 warps per SM, no
+// spills); the 256- and 128-thread builds take 24 and 20 warps per SM at 80
+// and 96 registers, with spills, and measured slower on node2vec.
 constexpr int min_ctas(int nt) { return nt >= 512 ? 1 : (nt >= 256 ? 3 : 5); }
 
 // SERVE: the served form's build (queries claimed from the request ring,

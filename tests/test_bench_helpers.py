@@ -42,3 +42,18 @@ def test_workloads_describe_their_inputs():
             assert "log-normal" in d
         if w.get("starts") == "maxdeg":
             assert "max-degree" in d
+
+
+def test_source_hash_ignores_comments_not_code(tmp_path, monkeypatch):
+    for f in bench.KERNEL_SOURCES:
+        (tmp_path / f).parent.mkdir(parents=True, exist_ok=True)
+        (tmp_path / f).write_text('int a = 1;  // one\n/* block */ const char* s = "x // y";\n')
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench.kernel_sources_hash()
+    f0 = tmp_path / bench.KERNEL_SOURCES[0]
+    f0.write_text('int a = 1;  // other words\n/* a longer\n   block */   const char* s = "x // y";\n')
+    assert bench.kernel_sources_hash() == h0          # comments and layout only
+    f0.write_text('int a = 2;  // one\n/* block */ const char* s = "x // y";\n')
+    assert bench.kernel_sources_hash() != h0          # code
+    f0.write_text('int a = 1;  // one\n/* block */ const char* s = "x // z";\n')
+    assert bench.kernel_sources_hash() != h0          # a string literal is code
